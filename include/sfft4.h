@@ -1,0 +1,212 @@
+/*
+ * sfft4.h -- C ABI of the GB300 (sm_103a) sFFT4.0 library.
+ *
+ * sFFT4.0 is the multiscale flat-window sparse FFT of Li, Jiang and Chen, "On Performance
+ * of Multiscale Sparse Fast Fourier Transform Algorithm" (arXiv 2011.05698).  Given a
+ * length-N signal whose spectrum is (approximately) K-sparse, it returns K (frequency,
+ * value) pairs while reading only a small fraction of the samples.
+ *
+ * Conventions (Section 2.1, Eq. 1-2): X_f = (1/N) sum_n x_n exp(-2 pi i f n / N); the
+ * values returned are these X_f (a unit-magnitude tone x_n = exp(2 pi i f n / N) returns
+ * X_f = 1).
+ *
+ * All entry points return 0 (SFFT4_OK) or a negative SFFT4_E* code; no exception or
+ * longjmp crosses the ABI.  Device pointers are caller-owned and must stay valid until the
+ * work queued on the given stream has completed.  Execution is asynchronous on the
+ * caller's stream (a cudaStream_t passed as void*; NULL = the legacy default stream).
+ * A plan is not thread-safe: do not execute one plan concurrently from two host threads
+ * or on two streams at once (its workspace is shared by all its executions).
+ */
+#ifndef SFFT4_H
+#define SFFT4_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SFFT4_API __attribute__((visibility("default")))
+#else
+#define SFFT4_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------------- error codes ---- */
+#define SFFT4_OK 0
+#define SFFT4_EINVAL (-1)   /* invalid argument (sizes, parameters, null pointers)      */
+#define SFFT4_ENOMEM (-2)   /* device or host allocation failed                        */
+#define SFFT4_ECUDA (-3)    /* a CUDA runtime call failed (details: sfft4_last_cuda_error) */
+#define SFFT4_ESTATE (-4)   /* call not valid in the plan's current state               */
+
+/* ----------------------------------------------------------------- precision ------ */
+#define SFFT4_FP32 0        /* window, fold and B-point DFT in FP32 (CUDA cores)         */
+#define SFFT4_BF16X3 1      /* B-point DFT as a BF16x3 split-precision complex GEMM on   */
+                            /* the tensor cores (tcgen05), FP32 accumulation             */
+
+typedef struct sfft4_plan_s* sfft4_plan_t;   /* opaque, library-owned */
+
+typedef struct {
+    double re, im;
+} sfft4_c128;
+
+/* Plan options; a zero field means "default".  Fill with sfft4_opts_default(). */
+typedef struct {
+    int32_t B1;              /* buckets of iteration 1 (power of two, 16..4096, <= N/64);
+                                default pow2ceil(2K) capped at min(4096, N/64)            */
+    double delta;            /* flat-window leakage delta of Eq. 9; default 1e-8          */
+    int32_t precision;       /* SFFT4_FP32 (default) or SFFT4_BF16X3                      */
+    int32_t min_votes;       /* levels that must vote to accept; default = all levels     */
+    double select_factor;    /* c in n_c = min(B_m, ceil(c max(K_m, 1))); default 2       */
+    double sig_floor;        /* candidate floor relative to max |yhat_0|^2 of iteration 1;
+                                default 1e-10; negative disables the floor                 */
+    double mag_tol;          /* magnitude consistency of a vote; default 0.5              */
+    int32_t max_iters;       /* cap on the static schedule length; default 64             */
+    int32_t max_batch;       /* most signals one sfft4_execute_batched call may pass;
+                                sizes the workspace; default 1                            */
+    int32_t trace;           /* nonzero: keep per-iteration bucket arrays and found sets
+                                of signal 0 for sfft4_trace_get (tests); default 0         */
+    int32_t profile;         /* nonzero: bracket each kernel launch of an execute with CUDA
+                                events on the execution stream (sfft4_profile_get)        */
+} sfft4_opts;
+
+/* Fills *opts with the defaults above.  Returns SFFT4_EINVAL if opts is NULL. */
+SFFT4_API int sfft4_opts_default(sfft4_opts* opts);
+
+/*
+ * sfft4_plan -- build the static plan of one transform size (Section 3.1, Lemma 2).
+ *   N     transform length, a power of two in [2^8, 2^30]
+ *   K     sparsity, 1 <= K <= min(4096, N/64)
+ *   l     multiscale parameter (blocks per level, Section 3.2), 2 <= l <= 32
+ *   q     extension parameter (Section 3.2), 0 <= q, l > q + 1; quantised to q_n/256
+ *   seed  key of the Philox4x64-10 draws of sigma and the per-iteration offset: signal i of a
+ *         batch, iteration m uses counter (i, m, 0, 0) and key (seed, 0)
+ *   opts  may be NULL (all defaults)
+ * On success *out owns device tables (window G and its spectrum for every bucket count of
+ * the schedule, FFT twiddles) and workspace for opts->max_batch signals.  The window tables
+ * are generated by kernels on the current CUDA device, synchronously.
+ * Errors: SFFT4_EINVAL (out NULL, N not a power of two or out of range, K out of range,
+ * l or q out of range, B1 invalid, delta not in (0, 1/2), window wider than N/2, or more
+ * than 64 rounds in an iteration), SFFT4_ENOMEM, SFFT4_ECUDA.
+ */
+SFFT4_API int sfft4_plan(sfft4_plan_t* out, int64_t N, int64_t K, int32_t l, double q, uint64_t seed,
+               const sfft4_opts* opts);
+
+/* Releases a plan (NULL is ignored).  Synchronises the device first. */
+SFFT4_API void sfft4_destroy(sfft4_plan_t plan);
+
+/*
+ * sfft4_execute -- one transform (signal index 0 of the Philox counter).
+ *   x_dev      N complex64 samples (interleaved re, im float32), device memory, 8-byte aligned
+ *   idx_dev    K int64 outputs: frequencies in [0, N) ascending; unused tail = -1
+ *   val_dev    K complex128 outputs X_f in the Eq. 2 normalisation; unused tail = 0
+ *   nfound_dev 1 int64 output: number of valid entries (<= K)
+ *   votes_dev  K int8 outputs (levels that voted when the frequency was first accepted),
+ *              may be NULL
+ *   stream     cudaStream_t or NULL
+ * Errors: SFFT4_EINVAL (NULL plan or output pointers), SFFT4_ECUDA (launch failure).
+ */
+SFFT4_API int sfft4_execute(sfft4_plan_t plan, const void* x_dev, int64_t* idx_dev, sfft4_c128* val_dev,
+                  int64_t* nfound_dev, int8_t* votes_dev, void* stream);
+
+/*
+ * sfft4_execute_batched -- nsig independent transforms of the plan's (N, K) in one pass
+ * of batched kernels; signal i uses Philox counter (i, m, 0, 0).
+ *   nsig        1 <= nsig <= opts.max_batch of the plan
+ *   x_dev       nsig * x_stride complex64 elements, device; signal i starts at
+ *               x_dev + i * x_stride (x_stride >= N, in complex elements)
+ *   idx_dev     nsig * K int64, val_dev nsig * K complex128, nfound_dev nsig int64,
+ *   votes_dev   nsig * K int8 (may be NULL); row i belongs to signal i
+ * Errors: SFFT4_EINVAL, SFFT4_ECUDA.
+ */
+SFFT4_API int sfft4_execute_batched(sfft4_plan_t plan, int32_t nsig, const void* x_dev, int64_t x_stride,
+                          int64_t* idx_dev, sfft4_c128* val_dev, int64_t* nfound_dev,
+                          int8_t* votes_dev, void* stream);
+
+/* ----------------------------------------------------------------- introspection -- */
+typedef struct {
+    int64_t N, K;
+    int32_t l, q_num;          /* q = q_num / 256 */
+    int32_t B1, n_iters, max_R, precision;
+    int64_t samples_per_transform;  /* distinct x positions read by one transform:
+                                       sum over iterations of |union_s [tau_s-h, tau_s+h]| */
+    int64_t found_capacity;    /* entries the found set of one signal can hold */
+    int32_t kernels_per_execute;  /* kernel launches of one execute (any batch size) */
+} sfft4_plan_info;
+
+/* Static plan summary.  Errors: SFFT4_EINVAL on NULL arguments. */
+SFFT4_API int sfft4_get_plan_info(sfft4_plan_t plan, sfft4_plan_info* info);
+
+#define SFFT4_MAX_ROUNDS 64
+typedef struct {
+    int32_t B;                 /* buckets B_m */
+    int32_t S;                 /* multiscale levels; rounds R = S + 1 */
+    int32_t n_c;               /* candidate buckets examined */
+    int32_t h;                 /* window half-width (w = 2h + 1) */
+    int64_t L;                 /* N / B_m */
+    int64_t Lbar[SFFT4_MAX_ROUNDS];   /* nominal level lengths, levels 1..S (index 0..S-1) */
+    int64_t tau[SFFT4_MAX_ROUNDS];    /* offsets tau_0 = 0 .. tau_S (index 0..S)           */
+    uint32_t H[SFFT4_MAX_ROUNDS];     /* vote thresholds in 2^-32 turns, levels 1..S      */
+    int64_t unique_samples;    /* |union_s [tau_s - h, tau_s + h]| */
+} sfft4_iter_info;
+
+/* Parameters of iteration m (1-based).  Errors: SFFT4_EINVAL (NULL or m out of range). */
+SFFT4_API int sfft4_get_iter_info(sfft4_plan_t plan, int32_t m, sfft4_iter_info* info);
+
+/*
+ * sfft4_get_window -- copies the window of bucket count B used by the plan to host memory:
+ * G (2h+1 float32 coefficients G_{-h..h}, as applied by the fold) and Ghat (3L/2 + 1
+ * float32 values of the spectrum G'^_k, k = 0..3L/2).  Either output may be NULL.
+ * Synchronous.  Errors: SFFT4_EINVAL (B not in the schedule), SFFT4_ECUDA.
+ */
+SFFT4_API int sfft4_get_window(sfft4_plan_t plan, int32_t B, float* G_host, float* Ghat_host);
+
+/*
+ * sfft4_bucketize -- frequency bucketization of one iteration alone (Lemma 1, Eq. 13):
+ * for signal index `signal` and iteration m, writes the R x B raw bucket arrays
+ * yhat_s[b] (complex64, row s = round s) to y_dev; no update, selection or location.
+ * Errors: SFFT4_EINVAL, SFFT4_ECUDA.
+ */
+SFFT4_API int sfft4_bucketize(sfft4_plan_t plan, const void* x_dev, int32_t signal, int32_t m,
+                    void* y_dev, void* stream);
+
+/*
+ * sfft4_trace_get -- after an execute on a plan made with opts.trace != 0, copies (to host,
+ * synchronously) for iteration m of signal 0: the raw R x B bucket arrays (complex64,
+ * y_host may be NULL) and the found set after the iteration: *nfound entries of
+ * frequency (f_host, int64), value (v_host, complex128) and votes (votes_host, int8),
+ * each of capacity `cap` entries (any of them may be NULL).
+ * Errors: SFFT4_ESTATE (plan not traced or not executed), SFFT4_EINVAL, SFFT4_ECUDA.
+ */
+SFFT4_API int sfft4_trace_get(sfft4_plan_t plan, int32_t m, void* y_host, int64_t cap, int64_t* f_host,
+                    sfft4_c128* v_host, int8_t* votes_host, int64_t* nfound);
+
+/*
+ * Kernel times of a profiled plan (opts.profile != 0), summed over the executes since the
+ * last reset: per kernel kind (fold = permuted gather + window + fold, fft = B-point DFT,
+ * decode = update/selection/location/estimation/merge, finalize) the number of launches
+ * and their total duration from CUDA events recorded on the execution stream around each
+ * launch; fold_samples counts the x samples the fold launches read (distinct positions per
+ * signal and iteration, times the signals).  Synchronises with the events; reset != 0
+ * clears the totals afterwards.
+ * Errors: SFFT4_EINVAL (NULL), SFFT4_ESTATE (plan not made with opts.profile), SFFT4_ECUDA.
+ */
+typedef struct {
+    int64_t fold_launches, fft_launches, decode_launches, finalize_launches;
+    double fold_ms, fft_ms, decode_ms, finalize_ms;
+    int64_t fold_samples;
+} sfft4_profile;
+
+SFFT4_API int sfft4_profile_get(sfft4_plan_t plan, sfft4_profile* out, int32_t reset);
+
+/* Text of an error code (static storage). */
+SFFT4_API const char* sfft4_strerror(int code);
+
+/* Text of the last CUDA error seen by this thread inside the library (static storage). */
+SFFT4_API const char* sfft4_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SFFT4_H */

@@ -143,7 +143,7 @@ def update(Y, found, N, B, L, sigma, offsets, Ghat):
 
 
 def select(Y0, n_c, theta):
-    """Candidate buckets: top n_c by |yhat_0|^2 (ties to the lower b), above theta (R11).
+    """Candidate buckets: top n_c by |yhat_0|^2 (ties to the lower b), strictly above theta (R11).
 
     Returns (sorted bucket indices, margin) where margin is the smallest relative gap
     of a selection decision (n_c-th vs next key, and keys vs theta)."""
@@ -151,7 +151,7 @@ def select(Y0, n_c, theta):
     B = key.shape[0]
     order = np.lexsort((np.arange(B), -key))
     top = order[:n_c]
-    keep = top[key[top] >= theta]
+    keep = top[key[top] > theta]
     gaps = [np.inf]
     if n_c < B:
         k1, k2 = key[order[n_c - 1]], key[order[n_c]]

@@ -1,0 +1,173 @@
+"""sFFT4.0 (multiscale flat-window sparse FFT, arXiv 2011.05698) on GB300 (sm_103a).
+
+A thin Python binding over the C ABI of libsfft4.so (include/sfft4.h).  Every step of
+the transform runs in the library's CUDA kernels; PyTorch only provides device memory and
+the current stream.  There is no CPU fallback: without the built library or a CUDA device
+every call raises.
+
+    plan = Plan(N=2**22, K=1000, l=16, q=1.0, seed=7, max_batch=64)
+    idx, val, nfound, votes = plan.execute(x)            # x: cuda complex64, length N
+    idx, val, nfound, votes = plan.execute_batched(xs)   # xs: cuda complex64, (nsig, N)
+"""
+
+import ctypes
+
+from . import _lib
+from ._lib import Sfft4Error, check  # noqa: F401
+
+__all__ = ["Plan", "Sfft4Error", "load"]
+
+
+def load():
+    return _lib.load()
+
+
+def _stream_ptr(device):
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+class Plan:
+    """A static sFFT4.0 plan (Section 3.1) for one (N, K, l, q, seed)."""
+
+    def __init__(self, N, K, l=16, q=1.0, seed=0, *, B1=0, delta=1e-8, precision="fp32",
+                 min_votes=0, select_factor=2.0, sig_floor=1e-10, mag_tol=0.5, max_iters=64,
+                 max_batch=1, trace=False, profile=False, device=None):
+        import torch
+        lib = _lib.load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("sFFT4 needs a CUDA device")
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        o = _lib.Opts()
+        check(lib.sfft4_opts_default(ctypes.byref(o)), "sfft4_opts_default")
+        o.B1 = B1
+        o.delta = delta
+        o.precision = {"fp32": _lib.SFFT4_FP32, "bf16x3": _lib.SFFT4_BF16X3}[precision]
+        o.min_votes = min_votes
+        o.select_factor = select_factor
+        o.sig_floor = sig_floor
+        o.mag_tol = mag_tol
+        o.max_iters = max_iters
+        o.max_batch = max_batch
+        o.trace = int(bool(trace))
+        o.profile = int(bool(profile))
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(lib.sfft4_plan(ctypes.byref(h), N, K, l, q, seed, ctypes.byref(o)), "sfft4_plan")
+        self._h = h
+        self.N, self.K, self.l, self.q, self.seed = N, K, l, q, seed
+        self.max_batch = max_batch
+        inf = _lib.PlanInfo()
+        check(lib.sfft4_get_plan_info(h, ctypes.byref(inf)), "sfft4_get_plan_info")
+        self.info = {k: getattr(inf, k) for k, _ in _lib.PlanInfo._fields_}
+
+    # ------------------------------------------------------------------ lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.load().sfft4_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------------ introspection
+    def iter_info(self, m):
+        it = _lib.IterInfo()
+        check(_lib.load().sfft4_get_iter_info(self._h, m, ctypes.byref(it)), "sfft4_get_iter_info")
+        S = it.S
+        return {"B": it.B, "S": S, "R": S + 1, "n_c": it.n_c, "h": it.h, "L": it.L,
+                "Lbar": list(it.Lbar[:S]), "tau": list(it.tau[:S + 1]), "H": list(it.H[:S]),
+                "unique_samples": it.unique_samples}
+
+    def window(self, B):
+        """(G, Ghat) host float32 arrays of bucket count B."""
+        import numpy as np
+        it = next(self.iter_info(m) for m in range(1, self.info["n_iters"] + 1)
+                  if self.iter_info(m)["B"] == B)
+        G = np.empty(2 * it["h"] + 1, np.float32)
+        Gh = np.empty(3 * it["L"] // 2 + 1, np.float32)
+        check(_lib.load().sfft4_get_window(self._h, B, G.ctypes.data_as(ctypes.c_void_p),
+                                           Gh.ctypes.data_as(ctypes.c_void_p)), "sfft4_get_window")
+        return G, Gh
+
+    def profile(self, reset=True):
+        """Per-kernel launch counts and CUDA-event times since the last reset (profile=True)."""
+        pr = _lib.Profile()
+        check(_lib.load().sfft4_profile_get(self._h, ctypes.byref(pr), int(bool(reset))), "sfft4_profile_get")
+        return {k: getattr(pr, k) for k, _ in _lib.Profile._fields_}
+
+    # ------------------------------------------------------------------ execution
+    def _outputs(self, nsig):
+        import torch
+        K, dev = self.K, self.device
+        idx = torch.empty((nsig, K), dtype=torch.int64, device=dev)
+        val = torch.empty((nsig, K), dtype=torch.complex128, device=dev)
+        nf = torch.empty((nsig,), dtype=torch.int64, device=dev)
+        votes = torch.empty((nsig, K), dtype=torch.int8, device=dev)
+        return idx, val, nf, votes
+
+    def _check_x(self, x, ndim):
+        import torch
+        if not isinstance(x, torch.Tensor) or x.device.type != "cuda" or x.dtype != torch.complex64:
+            raise TypeError("x must be a CUDA complex64 tensor")
+        if x.dim() != ndim or x.shape[-1] != self.N or x.stride(-1) != 1:
+            raise ValueError(f"x must have shape (..., {self.N}) and unit inner stride")
+
+    def execute(self, x, out=None):
+        """One transform of x (length-N complex64 on the plan's device)."""
+        self._check_x(x, 1)
+        idx, val, nf, votes = out if out is not None else self._outputs(1)
+        check(_lib.load().sfft4_execute(self._h, ctypes.c_void_p(x.data_ptr()),
+                                        ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(val.data_ptr()),
+                                        ctypes.c_void_p(nf.data_ptr()), ctypes.c_void_p(votes.data_ptr()),
+                                        _stream_ptr(self.device)), "sfft4_execute")
+        return idx[0], val[0], nf[0], votes[0]
+
+    def execute_batched(self, xs, out=None):
+        """Transforms of each row of xs (shape (nsig, N), complex64, on the device)."""
+        self._check_x(xs, 2)
+        nsig = xs.shape[0]
+        idx, val, nf, votes = out if out is not None else self._outputs(nsig)
+        check(_lib.load().sfft4_execute_batched(self._h, nsig, ctypes.c_void_p(xs.data_ptr()), xs.stride(0),
+                                                ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(val.data_ptr()),
+                                                ctypes.c_void_p(nf.data_ptr()), ctypes.c_void_p(votes.data_ptr()),
+                                                _stream_ptr(self.device)), "sfft4_execute_batched")
+        return idx, val, nf, votes
+
+    def bucketize(self, x, m, signal=0):
+        """Raw bucket arrays (R, B) of iteration m for Philox signal index `signal` (Lemma 1)."""
+        import torch
+        self._check_x(x, 1)
+        it = self.iter_info(m)
+        y = torch.empty((it["R"], it["B"]), dtype=torch.complex64, device=self.device)
+        check(_lib.load().sfft4_bucketize(self._h, ctypes.c_void_p(x.data_ptr()), signal, m,
+                                          ctypes.c_void_p(y.data_ptr()), _stream_ptr(self.device)),
+              "sfft4_bucketize")
+        return y
+
+    def trace(self, m):
+        """(raw buckets (R, B) complex64, found f, found v, found votes) after iteration m
+        of signal 0 of the last execute (plan made with trace=True)."""
+        import numpy as np
+        it = self.iter_info(m)
+        cap = self.info["found_capacity"]
+        y = np.empty((it["R"], it["B"]), np.complex64)
+        f = np.empty(cap, np.int64)
+        v = np.empty(cap, np.complex128)
+        vt = np.empty(cap, np.int8)
+        nf = ctypes.c_int64()
+        check(_lib.load().sfft4_trace_get(self._h, m, y.ctypes.data_as(ctypes.c_void_p), cap,
+                                          f.ctypes.data_as(ctypes.c_void_p), v.ctypes.data_as(ctypes.c_void_p),
+                                          vt.ctypes.data_as(ctypes.c_void_p), ctypes.byref(nf)),
+              "sfft4_trace_get")
+        n = nf.value
+        return y, f[:n], v[:n], vt[:n]

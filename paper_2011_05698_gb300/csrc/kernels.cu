@@ -1,0 +1,1040 @@
+// sm_103a kernels of the sFFT4.0 hot path and the execute entry points.
+//
+//   k_window_*  flat window G (FP64 generation, FP32 copy) and its spectrum G'^ (Eq. 9-10)
+//   k_fold      permuted int64-exact gather x[(sigma t + a) mod N], window multiply and fold
+//               into B slots for every round of one iteration (Lemma 1, steps P0-P3)
+//   k_fft       B-point DFT of every (signal, round) column, FP32 radix-2 (Lemma 1, P3)
+//   k_decode    bucket update (Section 3.1), large-bucket selection, multiscale location
+//               with votes (Section 3.2, Eq. 15-19), median estimation (Eq. 14) and merge
+//   k_finalize  top-K by |v| and sort by frequency
+//
+// Determinism: every reduction has a fixed order (per-thread sequential sums, fixed-order
+// sums over copies, radix-2 butterflies), and the bucket update accumulates in int64
+// fixed point with order-independent integer atomics, so repeated runs are bit-identical.
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+
+#include "sfft4_internal.cuh"
+
+namespace sfft4 {
+
+// ----------------------------------------------------------------- small helpers ----
+__device__ __forceinline__ float2 ld_stream(const float2* p) {
+    float2 v;
+    asm("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
+
+// (cos, sin) of 2 pi r / 2^n for 0 <= r < 2^n, with exactly representable sincospif
+// arguments: r = rh 2^12 + rl, angle = 2 pi rh / 2^(n-12) + 2 pi rl / 2^n.
+__device__ __forceinline__ float2 cis_2pi_frac(uint64_t r, int n) {
+    float s, c;
+    if (n <= 24) {
+        sincospif(ldexpf((float)r, 1 - n), &s, &c);
+        return make_float2(c, s);
+    }
+    float sa, ca, sb, cb;
+    sincospif(ldexpf((float)(r >> 12), 13 - n), &sa, &ca);
+    sincospif(ldexpf((float)(r & 4095u), 1 - n), &sb, &cb);
+    return make_float2(ca * cb - sa * sb, sa * cb + ca * sb);
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// ----------------------------------------------------------------- window -----------
+__global__ void k_window_time(double* g64, int64_t h, int64_t N, int64_t M, double s_t) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i > 2 * h) return;
+    int64_t j = i - h;
+    double x = (double)j / s_t;
+    double g = exp(-0.5 * x * x);
+    double D;
+    if (j == 0) {
+        D = (double)(2 * M + 1);
+    } else {
+        // Dirichlet kernel of the box |k| <= M: sin(pi (2M+1) j / N) / sin(pi j / N),
+        // integer arguments reduced mod 2N first
+        int64_t twoN = 2 * N;
+        int64_t r1 = (((2 * M + 1) * j) % twoN + twoN) % twoN;
+        int64_t r2 = ((j % twoN) + twoN) % twoN;
+        D = sinpi((double)r1 / (double)N) / sinpi((double)r2 / (double)N);
+    }
+    g64[i] = g * D;
+}
+
+__global__ void k_window_norm(const double* g64, int64_t w, float* G32) {
+    __shared__ double red[1024];
+    double s = 0;
+    for (int64_t i = threadIdx.x; i < w; i += blockDim.x) s += g64[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    double tot = red[0];
+    for (int64_t i = threadIdx.x; i < w; i += blockDim.x) G32[i] = (float)(g64[i] / tot);
+}
+
+// G'^_k = sum_{j=-h..h} G_j cos(2 pi k j / N), one warp per k, Kahan-compensated FP32
+// terms per lane, lanes combined in FP64.
+__global__ void k_window_spectrum(const float* G32, int64_t h, int64_t N, int n, int64_t nk,
+                                  float* Ghat) {
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (warp >= nk) return;
+    uint64_t k = (uint64_t)warp;
+    float sum = 0.f, comp = 0.f;
+    for (int64_t i = lane; i <= 2 * h; i += 32) {
+        int64_t j = i - h;
+        uint64_t r = (k * (uint64_t)j) & (uint64_t)(N - 1);
+        float term = G32[i] * cis_2pi_frac(r, n).x;
+        float yk = term - comp;
+        float t = sum + yk;
+        comp = (t - sum) - yk;
+        sum = t;
+    }
+    double tot = (double)sum - (double)comp;
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
+    if (lane == 0) Ghat[k] = (float)tot;
+}
+
+__global__ void k_twiddles(float2* tw, int B) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= B / 2) return;
+    double s, c;
+    sincospi(2.0 * (double)k / (double)B, &s, &c);
+    tw[k] = make_float2((float)c, (float)-s);
+}
+
+int build_window_tables(sfft4_plan_s* p, Window* w, double delta) {
+    int64_t N = p->N, L = w->L, h = w->h, wlen = 2 * h + 1;
+    double c = 0;
+    {
+        // same construction as the planner: s_t = B * 4 sqrt2 erfcinv(delta) / (2 pi)
+        double y = delta;
+        double x = sqrt(-log(y));
+        for (int i = 0; i < 100; ++i) {
+            double f = erfc(x) - y;
+            double d = -2.0 / sqrt(M_PI) * exp(-x * x);
+            double step = f / d;
+            x -= step;
+            if (fabs(step) <= 1e-17 * fabs(x)) break;
+        }
+        c = 4.0 * sqrt(2.0) * x;
+    }
+    double s_t = (double)w->B * c / (2.0 * M_PI);
+    int64_t M = (3 * L) / 4;
+    double* g64 = nullptr;
+    int rc = check_cuda(cudaMalloc(&g64, wlen * sizeof(double)));
+    if (rc) return rc;
+    int64_t nk = (3 * L) / 2 + 1;
+    rc = check_cuda(cudaMalloc(&w->G, wlen * sizeof(float)));
+    if (!rc) rc = check_cuda(cudaMalloc(&w->Ghat, nk * sizeof(float)));
+    if (!rc) rc = check_cuda(cudaMalloc(&w->tw, (w->B / 2) * sizeof(float2)));
+    if (rc) { cudaFree(g64); return rc; }
+    k_window_time<<<(unsigned)((wlen + 255) / 256), 256>>>(g64, h, N, M, s_t);
+    k_window_norm<<<1, 1024>>>(g64, wlen, w->G);
+    k_window_spectrum<<<(unsigned)((nk * 32 + 255) / 256), 256>>>(w->G, h, N, p->n, nk, w->Ghat);
+    k_twiddles<<<(w->B / 2 + 255) / 256, 256>>>(w->tw, w->B);
+    rc = check_cuda(cudaGetLastError());
+    if (!rc) rc = check_cuda(cudaDeviceSynchronize());
+    cudaFree(g64);
+    return rc;
+}
+
+// ----------------------------------------------------------------- fold -------------
+struct FoldArgs {
+    const float2* x;
+    int64_t x_stride;
+    float2* z;
+    int64_t z_stride;
+    uint64_t N, seed;
+    int32_t m, signal0, B, Wj, h;
+    const float* G;
+    FoldGroup g;
+    int64_t tau[kFoldRG];
+};
+
+constexpr int kFoldUnroll = 8;
+
+// One CTA = (signal, slice of Wj residues mod B); thread (jj, p) owns the samples
+// t = rho + k P B with rho = slice Wj + jj + p B, so its fold slot for round s,
+// (t - tau_s) mod B, is fixed: it accumulates in registers, then the P copies of each slot
+// are summed in a fixed order.  Each x sample is loaded once for all rounds whose window
+// covers it.
+template <int RG>
+__global__ void __launch_bounds__(512) k_fold(const FoldArgs a) {
+    __shared__ uint64_t s_par[2];
+    __shared__ float2 red[512];
+    const int tid = threadIdx.x;
+    const int Wj = a.Wj, B = a.B;
+    const int P = a.g.P;
+    const int jj = tid % Wj, p = tid / Wj;
+    const int sig = blockIdx.y;
+    if (tid == 0) {
+        uint64_t s, o;
+        permutation_draw(a.seed, (uint64_t)(a.signal0 + sig), (uint64_t)a.m, a.N, &s, &o);
+        s_par[0] = s;
+        s_par[1] = o;
+    }
+    __syncthreads();
+    const uint64_t sigma = s_par[0], aoff = s_par[1], mask = a.N - 1;
+    const int64_t PB = (int64_t)P * B;
+    const int64_t rho = (int64_t)blockIdx.x * Wj + jj + (int64_t)p * B;
+    const uint64_t step = (sigma * (uint64_t)PB) & mask;
+    const float2* __restrict__ x = a.x + (int64_t)sig * a.x_stride;
+    const float* __restrict__ G = a.G;
+    float2 acc[RG];
+#pragma unroll
+    for (int s = 0; s < RG; ++s) acc[s] = make_float2(0.f, 0.f);
+
+    for (int sg = 0; sg < a.g.nseg; ++sg) {
+        const int64_t t0 = a.g.t0[sg], t1 = a.g.t1[sg];
+        const uint32_t rm = a.g.mask[sg];
+        int64_t d = (rho - t0) % PB;
+        if (d < 0) d += PB;
+        const int64_t t = t0 + d;
+        if (t >= t1) continue;
+        const int cnt = (int)((t1 - t + PB - 1) / PB);
+        uint64_t idx = (sigma * (uint64_t)t + aoff) & mask;
+        int gb[RG];
+#pragma unroll
+        for (int s = 0; s < RG; ++s) gb[s] = (int)(t - a.tau[s] + a.h);
+        const int pbi = (int)PB;
+        for (int k = 0; k < cnt; k += kFoldUnroll) {
+            float2 v[kFoldUnroll];
+#pragma unroll
+            for (int u = 0; u < kFoldUnroll; ++u) {
+                v[u] = (k + u < cnt) ? ld_stream(x + idx) : make_float2(0.f, 0.f);
+                idx = (idx + step) & mask;
+            }
+#pragma unroll
+            for (int u = 0; u < kFoldUnroll; ++u) {
+                if (k + u < cnt) {
+#pragma unroll
+                    for (int s = 0; s < RG; ++s) {
+                        if ((rm >> s) & 1u) {
+                            const float gw = __ldg(G + gb[s] + (k + u) * pbi);
+                            acc[s].x = fmaf(gw, v[u].x, acc[s].x);
+                            acc[s].y = fmaf(gw, v[u].y, acc[s].y);
+                        }
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < RG; ++s) {
+        if (s < a.g.nr) {
+            red[tid] = acc[s];
+            __syncthreads();
+            if (p == 0) {
+                float2 sum = red[jj];
+                for (int pp = 1; pp < P; ++pp) {
+                    float2 o = red[jj + pp * Wj];
+                    sum.x += o.x;
+                    sum.y += o.y;
+                }
+                int64_t slot = ((int64_t)blockIdx.x * Wj + jj - a.tau[s]) % B;
+                if (slot < 0) slot += B;
+                a.z[(int64_t)sig * a.z_stride + (int64_t)(a.g.r0 + s) * B + slot] = sum;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ----------------------------------------------------------------- FFT --------------
+// Radix-2 decimation-in-time B-point DFT (unnormalised, e^{-2 pi i b j / B}) of
+// `cpc` columns per CTA in shared memory; column c = signal * R + round.
+__global__ void k_fft(const float2* __restrict__ z, float2* __restrict__ y, int B, int logB,
+                      const float2* __restrict__ tw, int64_t z_stride, int64_t y_stride, int R,
+                      int cpc, int ncols) {
+    extern __shared__ float2 sm[];
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int c0 = blockIdx.x * cpc;
+    const int ncol = min(cpc, ncols - c0);
+    for (int i = tid; i < ncol * B; i += T) {
+        int c = i >> logB, e = i & (B - 1);
+        int col = c0 + c;
+        int64_t base = (int64_t)(col / R) * z_stride + (int64_t)(col % R) * B;
+        sm[c * B + (__brev((unsigned)e) >> (32 - logB))] = z[base + e];
+    }
+    __syncthreads();
+    for (int ls = 0; ls < logB; ++ls) {
+        const int hs = 1 << ls;
+        for (int bf = tid; bf < ncol * (B >> 1); bf += T) {
+            int c = bf >> (logB - 1), k = bf & ((B >> 1) - 1);
+            int pos = k & (hs - 1), grp = k >> ls;
+            int i0 = c * B + grp * 2 * hs + pos, i1 = i0 + hs;
+            float2 w = tw[pos << (logB - 1 - ls)];
+            float2 a0 = sm[i0], b0 = sm[i1];
+            float2 bw = cmul(b0, w);
+            sm[i0] = make_float2(a0.x + bw.x, a0.y + bw.y);
+            sm[i1] = make_float2(a0.x - bw.x, a0.y - bw.y);
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < ncol * B; i += T) {
+        int c = i >> logB, e = i & (B - 1);
+        int col = c0 + c;
+        int64_t base = (int64_t)(col / R) * y_stride + (int64_t)(col % R) * B;
+        y[base + e] = sm[c * B + e];
+    }
+}
+
+// ----------------------------------------------------------------- block helpers ----
+// Exclusive scan of per-thread counts over a 1024-thread block; returns this thread's
+// offset and writes the total to *total (all threads).
+__device__ int block_exscan(int v, int* warp_sums, int* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) warp_sums[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        int ws = warp_sums[lane];
+        int wi = ws;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        warp_sums[lane] = wi - ws;
+        if (lane == 31) warp_sums[32] = wi;
+    }
+    __syncthreads();
+    int res = warp_sums[wid] + inc - v;
+    *total = warp_sums[32];
+    __syncthreads();
+    return res;
+}
+
+__device__ int block_count(int v, int* slot) {
+    int w = __reduce_add_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0) atomicAdd(slot, w);
+    __syncthreads();
+    int r = *slot;
+    __syncthreads();
+    if (threadIdx.x == 0) *slot = 0;
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ uint32_t hash_slot(int32_t f, int Hlog) {
+    return ((uint32_t)f * 2654435761u) >> (32 - Hlog);
+}
+
+__device__ int32_t hash_find(const int32_t* keys, const int32_t* vals, int Hlog, int32_t f) {
+    const uint32_t msk = (1u << Hlog) - 1;
+    uint32_t s = hash_slot(f, Hlog);
+    for (uint32_t probe = 0; probe <= msk; ++probe) {
+        int32_t k = keys[s];
+        if (k == f) return vals[s];
+        if (k == -1) return -1;
+        s = (s + 1) & msk;
+    }
+    return -1;
+}
+
+__device__ void hash_insert(int32_t* keys, int32_t* vals, int Hlog, int32_t f, int32_t idx) {
+    const uint32_t msk = (1u << Hlog) - 1;
+    uint32_t s = hash_slot(f, Hlog);
+    for (uint32_t probe = 0; probe <= msk; ++probe) {
+        int32_t prev = atomicCAS(&keys[s], -1, f);
+        if (prev == -1) {
+            vals[s] = idx;
+            return;
+        }
+        s = (s + 1) & msk;
+    }
+}
+
+// ----------------------------------------------------------------- decode -----------
+struct DecodeArgs {
+    uint64_t N, seed;
+    int32_t n, signal0, first, l, qn, min_votes;
+    float mag_tol, sig_floor;
+    const IterDev* it;
+    float2* y;
+    int64_t y_stride;
+    int32_t* F;
+    int32_t* ff;
+    double2* fv;
+    int8_t* fvotes;
+    int64_t Fcap;
+    int32_t* hkeys;
+    int32_t* hvals;
+    int32_t Hlog;
+    float* theta;
+    int32_t* fxexp;
+};
+
+__device__ __forceinline__ float med_sorted(float* v, int R) {
+    for (int i = 1; i < R; ++i) {
+        float x = v[i];
+        int j = i - 1;
+        while (j >= 0 && v[j] > x) {
+            v[j + 1] = v[j];
+            --j;
+        }
+        v[j + 1] = x;
+    }
+    return (R & 1) ? v[R / 2] : 0.5f * (v[R / 2 - 1] + v[R / 2]);
+}
+
+// One CTA per signal: update the bucket arrays by the found set, select the large
+// buckets, locate each candidate by the multiscale method, vote, estimate and merge.
+__global__ void __launch_bounds__(kDecodeThreads) k_decode(const DecodeArgs a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ uint64_t s_par[3];
+    __shared__ int s_ws[33];
+    __shared__ int s_cnt;
+    __shared__ unsigned s_max;
+    __shared__ float s_theta;
+    __shared__ int s_fx;
+    const IterDev* __restrict__ it = a.it;
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int sig = blockIdx.x;
+    const int B = it->B, R = it->R, S = it->S, logL = it->logL;
+    const int64_t L = it->L;
+    const uint64_t N = a.N, mask = N - 1;
+    const int n = a.n, shift = 32 - n;
+    float2* Y = a.y + (int64_t)sig * a.y_stride;
+    int32_t* ff = a.ff + (int64_t)sig * a.Fcap;
+    double2* fv = a.fv + (int64_t)sig * a.Fcap;
+    int8_t* fvotes = a.fvotes + (int64_t)sig * a.Fcap;
+    int32_t* hk = a.hkeys + ((int64_t)sig << a.Hlog);
+    int32_t* hv = a.hvals + ((int64_t)sig << a.Hlog);
+    if (tid == 0) {
+        uint64_t s, o;
+        permutation_draw(a.seed, (uint64_t)(a.signal0 + sig), (uint64_t)it->m, N, &s, &o);
+        s_par[0] = s;
+        s_par[1] = o;
+        s_par[2] = inv_odd64(s) & mask;
+        s_cnt = 0;
+        s_max = 0;
+        s_fx = a.first ? 0 : a.fxexp[sig];
+    }
+    __syncthreads();
+    const uint64_t sigma = s_par[0], aoff = s_par[1], sinv = s_par[2];
+    const int F0 = a.F[sig];
+
+    // shared memory (bytes, 26 B in total): [0, 16B) the update's int64 accumulators, later
+    // reused for candidate results (frequency [0,4B), value [4B,12B), votes [12B,13B));
+    // keys [16B,20B); candidate list [20B,22B); found-set lookups [22B,26B)
+    long long* acc = (long long*)smraw;
+    int32_t* cf = (int32_t*)smraw;
+    float2* cv = (float2*)(smraw + 4 * (size_t)B);
+    int8_t* cvt = (int8_t*)(smraw + 12 * (size_t)B);
+    float* key = (float*)(smraw + 16 * (size_t)B);
+    uint16_t* cand = (uint16_t*)(smraw + 20 * (size_t)B);
+    int32_t* cexist = (int32_t*)(smraw + 22 * (size_t)B);
+
+    // ---- 1. update: yhat' = yhat - yhat_update, round by round (Section 3.1) ----------
+    // Contributions of the found coefficients are accumulated in int64 fixed point
+    // (2^(fx-40) units, fx = exponent of the largest bucket of iteration 1) with integer
+    // atomics, so the result does not depend on the order of the additions.
+    if (!a.first && F0 > 0) {
+        const int fx = s_fx;
+        const float scale = ldexpf(1.f, 40 - fx);
+        const float iscale = ldexpf(1.f, fx - 40);
+        for (int r = 0; r < R; ++r) {
+            for (int i = tid; i < 2 * B; i += T) acc[i] = 0;
+            __syncthreads();
+            const uint64_t o_r = (aoff + sigma * (uint64_t)it->tau[r]) & mask;
+            for (int i = tid; i < F0; i += T) {
+                const uint64_t f = (uint64_t)ff[i];
+                const double2 vd = fv[i];
+                const float2 v = make_float2((float)vd.x, (float)vd.y);
+                const uint64_t u = (sigma * f) & mask;
+                const int b0 = (int)(((u + (uint64_t)(L >> 1)) >> logL) & (uint64_t)(B - 1));
+                const float2 c = cmul(v, cis_2pi_frac((f * o_r) & mask, n));
+#pragma unroll
+                for (int db = -1; db <= 1; ++db) {
+                    const int b = (b0 + db) & (B - 1);
+                    const int64_t k = (int64_t)((((uint64_t)b * (uint64_t)L - u) + (N >> 1)) & mask) -
+                                      (int64_t)(N >> 1);
+                    const float g = it->Ghat[k < 0 ? -k : k];
+                    atomicAdd((unsigned long long*)&acc[2 * b], (unsigned long long)__float2ll_rn(g * c.x * scale));
+                    atomicAdd((unsigned long long*)&acc[2 * b + 1], (unsigned long long)__float2ll_rn(g * c.y * scale));
+                }
+            }
+            __syncthreads();
+            for (int b = tid; b < B; b += T) {
+                float2 yv = Y[(int64_t)r * B + b];
+                yv.x -= __ll2float_rn(acc[2 * b]) * iscale;
+                yv.y -= __ll2float_rn(acc[2 * b + 1]) * iscale;
+                Y[(int64_t)r * B + b] = yv;
+            }
+            __syncthreads();
+        }
+    }
+
+    // ---- 2. large-bucket selection (Section 3: buckets with p >= 1) -------------------
+    float mx = 0.f;
+    for (int b = tid; b < B; b += T) {
+        float2 y0 = Y[b];
+        float k2 = fmaf(y0.x, y0.x, y0.y * y0.y);
+        key[b] = k2;
+        mx = fmaxf(mx, k2);
+    }
+    if (a.first) {
+        const unsigned wm = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
+        if ((tid & 31) == 0) atomicMax(&s_max, wm);
+        __syncthreads();
+        if (tid == 0) {
+            const float m = __uint_as_float(s_max);
+            const float th = a.sig_floor > 0.f ? a.sig_floor * m : -1.f;
+            int e = 0;
+            frexpf(sqrtf(m), &e);
+            a.theta[sig] = th;
+            a.fxexp[sig] = e;
+            s_theta = th;
+        }
+    } else if (tid == 0) {
+        s_theta = a.theta[sig];
+    }
+    __syncthreads();
+    const float theta = s_theta;
+    const int n_c = it->n_c;
+    // threshold T = bits of the n_c-th largest key (keys >= 0 compare as unsigned)
+    uint32_t Tb = 0;
+    if (n_c < B) {
+        for (int bit = 30; bit >= 0; --bit) {
+            const uint32_t trial = Tb | (1u << bit);
+            int c = 0;
+            for (int b = tid; b < B; b += T) c += (__float_as_uint(key[b]) >= trial);
+            int tot = block_count(c, &s_cnt);
+            if (tot >= n_c) Tb = trial;
+        }
+    }
+    // each thread owns a contiguous chunk of buckets for order-preserving scans
+    const int E = (B + T - 1) / T;
+    const int b_lo = min(B, tid * E), b_hi = min(B, b_lo + E);
+    int need_ties = 0;
+    if (n_c < B) {
+        int gt = 0;
+        for (int b = tid; b < B; b += T) gt += (__float_as_uint(key[b]) > Tb);
+        need_ties = n_c - block_count(gt, &s_cnt);
+    }
+    // selection flags of this thread's chunk (E <= 4 buckets), ties to the lower b
+    int ties = 0;
+    for (int b = b_lo; b < b_hi; ++b) ties += (n_c < B && __float_as_uint(key[b]) == Tb);
+    int tot_ties;
+    int tie_rank = block_exscan(ties, s_ws, &tot_ties);
+    uint32_t selmask = 0;
+    int nsel_local = 0;
+    for (int b = b_lo; b < b_hi; ++b) {
+        const uint32_t kb = __float_as_uint(key[b]);
+        bool sel;
+        if (n_c >= B) sel = true;
+        else if (kb > Tb) sel = true;
+        else if (kb == Tb) { sel = tie_rank < need_ties; ++tie_rank; }
+        else sel = false;
+        sel = sel && (key[b] > theta);
+        if (sel) selmask |= 1u << (b - b_lo);
+        nsel_local += sel;
+    }
+    int ncand;
+    int pos = block_exscan(nsel_local, s_ws, &ncand);
+    for (int b = b_lo; b < b_hi; ++b)
+        if ((selmask >> (b - b_lo)) & 1u) cand[pos++] = (uint16_t)b;
+    __syncthreads();
+
+    // ---- 3. multiscale location, votes, estimation: one thread per candidate ----------
+    const int l = a.l, qn = a.qn;
+    const int need = a.min_votes > 0 ? min(a.min_votes, S) : S;
+    for (int ci = tid; ci < ncand; ci += T) {
+        const int b = cand[ci];
+        const float2 y0 = Y[b];
+        const float m0 = fmaf(y0.x, y0.x, y0.y * y0.y);
+        uint32_t Phi[kMaxRounds];
+        for (int s = 1; s <= S; ++s) {
+            const float2 ys = Y[(int64_t)s * B + b];
+            const float cr = ys.x * y0.x + ys.y * y0.y;
+            const float cim = ys.y * y0.x - ys.x * y0.y;
+            const float turns = atan2f(cim, cr) * 0.15915494309189535f;
+            Phi[s - 1] = (uint32_t)__float2ll_rn(turns * 4294967296.0f);
+        }
+        int64_t umin = (int64_t)b * L - L;
+        for (int s = 1; s < S; ++s) {
+            const uint64_t ts = (uint64_t)it->tau[s];
+            const uint64_t W = it->W[s - 1];
+            const uint32_t Ap = (uint32_t)((((uint64_t)umin & mask) * ts & mask) << shift);
+            const uint32_t ph = Phi[s - 1];
+            const uint32_t delta = ph - Ap;
+            const int64_t j0 = (int64_t)(((uint64_t)delta * (uint64_t)l) / W);
+            uint32_t bd = 0xffffffffu;
+            int bj = l;
+            const int64_t cands[5] = {j0 - 1, j0, j0 + 1, 0, l - 1};
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                const int64_t j = cands[q];
+                if (j < 0 || j >= l) continue;
+                const uint32_t Ej = Ap + (uint32_t)(((uint64_t)(2 * j + 1) * W + (uint64_t)l) / (uint64_t)(2 * l));
+                const uint32_t d = circ_dist(ph, Ej);
+                if (d < bd || (d == bd && j < bj)) { bd = d; bj = (int)j; }
+            }
+            const int64_t Lb = it->Lbar[s - 1];
+            umin += floor_div(((int64_t)2 * bj * kQDen - qn) * Lb, (int64_t)2 * l * kQDen);
+        }
+        // final level: the Lbar_S integers u_min + i
+        uint64_t ustar;
+        {
+            const uint64_t ts = (uint64_t)it->tau[S];
+            const int64_t Lb = it->Lbar[S - 1];
+            const uint32_t Dl = (uint32_t)it->W[S - 1];
+            const uint32_t P0 = (uint32_t)((((uint64_t)umin & mask) * ts & mask) << shift);
+            const uint32_t ph = Phi[S - 1];
+            const int64_t i0 = (int64_t)((uint32_t)(ph - P0) / Dl);
+            uint32_t bd = 0xffffffffu;
+            int64_t bi = Lb;
+            const int64_t cands[5] = {i0 - 1, i0, i0 + 1, 0, Lb - 1};
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                const int64_t i = cands[q];
+                if (i < 0 || i >= Lb) continue;
+                const uint32_t Pi = P0 + (uint32_t)((uint64_t)i * Dl);
+                const uint32_t d = circ_dist(ph, Pi);
+                if (d < bd || (d == bd && i < bi)) { bd = d; bi = i; }
+            }
+            ustar = (uint64_t)(umin + bi) & mask;
+        }
+        int votes = 0;
+        for (int s = 1; s <= S; ++s) {
+            const uint32_t Ps = (uint32_t)(((ustar * (uint64_t)it->tau[s]) & mask) << shift);
+            const uint32_t d = circ_dist(Phi[s - 1], Ps);
+            const float2 ys = Y[(int64_t)s * B + b];
+            const float ms = fmaf(ys.x, ys.x, ys.y * ys.y);
+            votes += (d <= it->H[s - 1]) && (fabsf(ms - m0) <= a.mag_tol * m0);
+        }
+        const int own = (int)(((ustar + (uint64_t)(L >> 1)) >> logL) & (uint64_t)(B - 1)) == b;
+        const bool accept = votes >= need && own;
+        cvt[ci] = accept ? (int8_t)votes : (int8_t)-1;
+        if (accept) {
+            const uint64_t f = (sinv * ustar) & mask;
+            const int64_t kb = (int64_t)((((uint64_t)b * (uint64_t)L - ustar) + (N >> 1)) & mask) - (int64_t)(N >> 1);
+            const float g = it->Ghat[kb < 0 ? -kb : kb];
+            const float ig = 1.f / g;
+            float vre[kMaxRounds], vim[kMaxRounds];
+            for (int r = 0; r < R; ++r) {
+                const uint64_t o_r = (aoff + sigma * (uint64_t)it->tau[r]) & mask;
+                const float2 e = cis_2pi_frac((f * o_r) & mask, n);
+                const float2 yr = Y[(int64_t)r * B + b];
+                const float2 v = cmul(yr, make_float2(e.x, -e.y));
+                vre[r] = v.x * ig;
+                vim[r] = v.y * ig;
+            }
+            cf[ci] = (int32_t)f;
+            cv[ci] = make_float2(med_sorted(vre, R), med_sorted(vim, R));
+        }
+    }
+    __syncthreads();
+
+    // ---- 4. merge: x^m = x^{m-1} + x'^m (Section 3.1, step 5) -------------------------
+    for (int ci = tid; ci < ncand; ci += T)
+        cexist[ci] = (cvt[ci] >= 0) ? hash_find(hk, hv, a.Hlog, cf[ci]) : -2;
+    __syncthreads();
+    const int cE = (ncand + T - 1) / T;
+    const int c_lo = min(ncand, tid * cE), c_hi = min(ncand, c_lo + cE);
+    int nnew_local = 0;
+    for (int ci = c_lo; ci < c_hi; ++ci) nnew_local += (cexist[ci] == -1);
+    int nnew;
+    int npos = block_exscan(nnew_local, s_ws, &nnew);
+    for (int ci = c_lo; ci < c_hi; ++ci) {
+        const int ex = cexist[ci];
+        if (ex >= 0) {
+            double2 v = fv[ex];
+            v.x += (double)cv[ci].x;
+            v.y += (double)cv[ci].y;
+            fv[ex] = v;
+        } else if (ex == -1) {
+            const int e = F0 + npos++;
+            ff[e] = cf[ci];
+            fv[e] = make_double2((double)cv[ci].x, (double)cv[ci].y);
+            fvotes[e] = cvt[ci];
+            hash_insert(hk, hv, a.Hlog, cf[ci], e);
+        }
+    }
+    if (tid == 0) a.F[sig] = F0 + nnew;
+}
+
+
+// ----------------------------------------------------------------- finalize ---------
+// Top-K of the found set by |v| (ties to the lower frequency), sorted by frequency.
+__global__ void __launch_bounds__(1024) k_finalize(const int32_t* Fc, const int32_t* ffa,
+                                                   const double2* fva, const int8_t* fvta,
+                                                   int64_t Fcap, int64_t K, int64_t* idx_out,
+                                                   sfft4_c128* val_out, int64_t* nfound_out,
+                                                   int8_t* votes_out) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    unsigned long long* srt = (unsigned long long*)smraw;  // (f << 32 | entry), pow2 >= K
+    __shared__ int s_cnt;
+    __shared__ int s_ws[33];
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int sig = blockIdx.x;
+    const int F0 = Fc[sig];
+    const int32_t* ff = ffa + (int64_t)sig * Fcap;
+    const double2* fv = fva + (int64_t)sig * Fcap;
+    const int8_t* fvt = fvta + (int64_t)sig * Fcap;
+    if (tid == 0) s_cnt = 0;
+    __syncthreads();
+    auto keyof = [&](int i) -> unsigned long long {
+        const double2 v = fv[i];
+        return (unsigned long long)__double_as_longlong(v.x * v.x + v.y * v.y);
+    };
+    unsigned long long Tk = 0;
+    int32_t fT = 0x7fffffff;
+    const bool cut = F0 > K;
+    if (cut) {
+        for (int bit = 62; bit >= 0; --bit) {
+            const unsigned long long trial = Tk | (1ull << bit);
+            int c = 0;
+            for (int i = tid; i < F0; i += T) c += keyof(i) >= trial;
+            if (block_count(c, &s_cnt) >= K) Tk = trial;
+        }
+        int gt = 0;
+        for (int i = tid; i < F0; i += T) gt += keyof(i) > Tk;
+        const int need = (int)K - block_count(gt, &s_cnt);
+        // among ties at Tk keep the `need` lowest frequencies
+        int32_t lo = 0;
+        for (int bit = 30; bit >= 0; --bit) {
+            const int32_t trial = lo | (1 << bit);
+            int c = 0;
+            for (int i = tid; i < F0; i += T) c += (keyof(i) == Tk) && (ff[i] < trial);
+            if (block_count(c, &s_cnt) < need) lo = trial;
+        }
+        fT = lo;  // ties with f <= fT are kept
+    }
+    const int E = (F0 + T - 1) / T;
+    const int e_lo = min(F0, tid * E), e_hi = min(F0, e_lo + E);
+    int nl = 0;
+    for (int i = e_lo; i < e_hi; ++i) {
+        const unsigned long long k = keyof(i);
+        nl += !cut || k > Tk || (k == Tk && ff[i] <= fT);
+    }
+    int nsel;
+    int pos = block_exscan(nl, s_ws, &nsel);
+    int P2 = 1;
+    while (P2 < nsel) P2 <<= 1;
+    for (int i = tid; i < P2; i += T) srt[i] = ~0ull;
+    __syncthreads();
+    for (int i = e_lo; i < e_hi; ++i) {
+        const unsigned long long k = keyof(i);
+        if (!cut || k > Tk || (k == Tk && ff[i] <= fT))
+            srt[pos++] = ((unsigned long long)(uint32_t)ff[i] << 32) | (uint32_t)i;
+    }
+    __syncthreads();
+    for (int kk = 2; kk <= P2; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < P2; i += T) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const unsigned long long a0 = srt[i], b0 = srt[ixj];
+                    const bool up = (i & kk) == 0;
+                    if ((a0 > b0) == up) { srt[i] = b0; srt[ixj] = a0; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = tid; i < K; i += T) {
+        const int64_t o = (int64_t)sig * K + i;
+        if (i < nsel) {
+            const int e = (int)(srt[i] & 0xffffffffu);
+            idx_out[o] = (int64_t)(srt[i] >> 32);
+            val_out[o].re = fv[e].x;
+            val_out[o].im = fv[e].y;
+            if (votes_out) votes_out[o] = fvt[e];
+        } else {
+            idx_out[o] = -1;
+            val_out[o].re = 0;
+            val_out[o].im = 0;
+            if (votes_out) votes_out[o] = 0;
+        }
+    }
+    if (tid == 0) nfound_out[sig] = nsel;
+}
+
+// ----------------------------------------------------------------- launchers --------
+int launch_bucketize(sfft4_plan_s* p, int mi, int nsig, const float2* x, int64_t x_stride,
+                     int32_t signal0, float2* y_out, int64_t y_sig_stride, cudaStream_t st) {
+    const IterHost& ih = p->iters[mi];
+    const IterDev& d = ih.d;
+    for (const FoldGroup& g : ih.groups) {
+        FoldArgs a;
+        a.x = x;
+        a.x_stride = x_stride;
+        a.z = p->z;
+        a.z_stride = (int64_t)p->R_max * p->B_max;
+        a.N = (uint64_t)p->N;
+        a.seed = p->seed;
+        a.m = d.m;
+        a.signal0 = signal0;
+        a.B = d.B;
+        a.Wj = ih.Wj;
+        a.h = d.h;
+        a.G = d.G;
+        a.g = g;
+        for (int s = 0; s < kFoldRG; ++s) a.tau[s] = (s < g.nr) ? d.tau[g.r0 + s] : 0;
+        dim3 grid(d.B / ih.Wj, nsig);
+        int threads = ih.Wj * g.P;
+        cudaEvent_t ev = nullptr;
+        int rc = prof_begin(p, st, &ev);
+        if (rc) return rc;
+        if (g.nr <= 4) k_fold<4><<<grid, threads, 0, st>>>(a);
+        else k_fold<8><<<grid, threads, 0, st>>>(a);
+        rc = prof_end(p, st, ev, kProfFold, g.unique * nsig);
+        if (rc) return rc;
+    }
+    // B-point DFT of every (signal, round) column
+    const int B = d.B, logB = d.logB, R = d.R;
+    int T = std::min(1024, std::max(256, B / 2));
+    int cpc = std::max(1, (2 * T) / B);
+    int ncols = nsig * R;
+    int blocks = (ncols + cpc - 1) / cpc;
+    size_t smem = (size_t)cpc * B * sizeof(float2);
+    cudaEvent_t ev = nullptr;
+    int rc = prof_begin(p, st, &ev);
+    if (rc) return rc;
+    k_fft<<<blocks, T, smem, st>>>(p->z, y_out, B, logB, d.tw, (int64_t)p->R_max * p->B_max,
+                                   y_sig_stride, R, cpc, ncols);
+    rc = check_cuda(cudaGetLastError());
+    if (rc) return rc;
+    return prof_end(p, st, ev, kProfFft, 0);
+}
+
+int launch_decode(sfft4_plan_s* p, int mi, int nsig, cudaStream_t st) {
+    const IterDev& d = p->iters[mi].d;
+    DecodeArgs a;
+    a.N = (uint64_t)p->N;
+    a.seed = p->seed;
+    a.n = p->n;
+    a.signal0 = 0;
+    a.first = (mi == 0);
+    a.l = p->l;
+    a.qn = p->qn;
+    a.min_votes = p->o.min_votes;
+    a.mag_tol = (float)p->o.mag_tol;
+    a.sig_floor = (float)p->o.sig_floor;
+    a.it = p->iters_dev + mi;
+    a.y = p->y;
+    a.y_stride = (int64_t)p->R_max * p->B_max;
+    a.F = p->F;
+    a.ff = p->ff;
+    a.fv = p->fv;
+    a.fvotes = p->fvotes;
+    a.Fcap = p->Fcap;
+    a.hkeys = p->hkeys;
+    a.hvals = p->hvals;
+    a.Hlog = p->Hlog;
+    a.theta = p->theta;
+    a.fxexp = p->fxexp;
+    size_t smem = 26 * (size_t)d.B;
+    cudaEvent_t ev = nullptr;
+    int rc = prof_begin(p, st, &ev);
+    if (rc) return rc;
+    k_decode<<<nsig, kDecodeThreads, smem, st>>>(a);
+    rc = check_cuda(cudaGetLastError());
+    if (rc) return rc;
+    return prof_end(p, st, ev, kProfDecode, 0);
+}
+
+int launch_finalize(sfft4_plan_s* p, int nsig, int64_t* idx, sfft4_c128* val, int64_t* nfound,
+                    int8_t* votes, cudaStream_t st) {
+    int P2 = 1;
+    while (P2 < p->K) P2 <<= 1;
+    size_t smem = (size_t)P2 * sizeof(unsigned long long);
+    cudaEvent_t ev = nullptr;
+    int rc = prof_begin(p, st, &ev);
+    if (rc) return rc;
+    k_finalize<<<nsig, 1024, smem, st>>>(p->F, p->ff, p->fv, p->fvotes, p->Fcap, p->K, idx, val,
+                                         nfound, votes);
+    rc = check_cuda(cudaGetLastError());
+    if (rc) return rc;
+    return prof_end(p, st, ev, kProfFinalize, 0);
+}
+
+int launch_reset(sfft4_plan_s* p, int nsig, cudaStream_t st) {
+    int rc = check_cuda(cudaMemsetAsync(p->F, 0, nsig * sizeof(int32_t), st));
+    if (rc) return rc;
+    return check_cuda(cudaMemsetAsync(p->hkeys, 0xff, ((size_t)nsig << p->Hlog) * sizeof(int32_t), st));
+}
+
+static int next_event(sfft4_plan_s* p, cudaEvent_t* e) {
+    if (p->ev_used == p->ev_pool.size()) {
+        cudaEvent_t ne;
+        int rc = check_cuda(cudaEventCreate(&ne));
+        if (rc) return rc;
+        p->ev_pool.push_back(ne);
+    }
+    *e = p->ev_pool[p->ev_used++];
+    return SFFT4_OK;
+}
+
+int prof_begin(sfft4_plan_s* p, cudaStream_t st, cudaEvent_t* a) {
+    if (!p->o.profile) return SFFT4_OK;
+    int rc = next_event(p, a);
+    if (rc) return rc;
+    return check_cuda(cudaEventRecord(*a, st));
+}
+
+int prof_end(sfft4_plan_s* p, cudaStream_t st, cudaEvent_t a, int kind, int64_t samples) {
+    if (!p->o.profile) return SFFT4_OK;
+    cudaEvent_t b;
+    int rc = next_event(p, &b);
+    if (rc) return rc;
+    rc = check_cuda(cudaEventRecord(b, st));
+    if (rc) return rc;
+    p->prof.push_back({a, b, kind, samples});
+    return SFFT4_OK;
+}
+
+int configure_kernels() {
+    static bool done = false;
+    if (done) return SFFT4_OK;
+    int rc = check_cuda(cudaFuncSetAttribute(k_decode, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             26 * kBMax));
+    if (!rc) rc = check_cuda(cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  8 * kKMax));
+    if (!rc) done = true;
+    return rc;
+}
+
+}  // namespace sfft4
+
+using namespace sfft4;
+
+namespace {
+int run(sfft4_plan_s* p, int nsig, const float2* x, int64_t x_stride, int64_t* idx,
+        sfft4_c128* val, int64_t* nfound, int8_t* votes, cudaStream_t st) {
+    int rc = configure_kernels();
+    if (rc) return rc;
+    rc = launch_reset(p, nsig, st);
+    if (rc) return rc;
+    const int64_t rb = (int64_t)p->R_max * p->B_max;
+    for (size_t mi = 0; mi < p->iters.size(); ++mi) {
+        rc = launch_bucketize(p, (int)mi, nsig, x, x_stride, 0, p->y, rb, st);
+        if (rc) return rc;
+        const IterDev& d = p->iters[mi].d;
+        if (p->o.trace) {
+            rc = check_cuda(cudaMemcpyAsync(p->trace_y + mi * rb, p->y, (size_t)d.R * d.B * sizeof(float2),
+                                            cudaMemcpyDeviceToDevice, st));
+            if (rc) return rc;
+        }
+        rc = launch_decode(p, (int)mi, nsig, st);
+        if (rc) return rc;
+        if (p->o.trace) {
+            rc = check_cuda(cudaMemcpyAsync(p->trace_F + mi, p->F, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+            if (!rc) rc = check_cuda(cudaMemcpyAsync(p->trace_ff + mi * p->Fcap, p->ff, p->Fcap * sizeof(int32_t),
+                                                     cudaMemcpyDeviceToDevice, st));
+            if (!rc) rc = check_cuda(cudaMemcpyAsync(p->trace_fv + mi * p->Fcap, p->fv, p->Fcap * sizeof(double2),
+                                                     cudaMemcpyDeviceToDevice, st));
+            if (!rc) rc = check_cuda(cudaMemcpyAsync(p->trace_votes + mi * p->Fcap, p->fvotes, p->Fcap,
+                                                     cudaMemcpyDeviceToDevice, st));
+            if (rc) return rc;
+        }
+    }
+    rc = launch_finalize(p, nsig, idx, val, nfound, votes, st);
+    if (!rc) p->executed = true;
+    return rc;
+}
+}  // namespace
+
+extern "C" {
+
+int sfft4_execute(sfft4_plan_t p, const void* x_dev, int64_t* idx_dev, sfft4_c128* val_dev,
+                  int64_t* nfound_dev, int8_t* votes_dev, void* stream) {
+    if (!p || !x_dev || !idx_dev || !val_dev || !nfound_dev) return SFFT4_EINVAL;
+    return run(p, 1, (const float2*)x_dev, p->N, idx_dev, val_dev, nfound_dev, votes_dev,
+               (cudaStream_t)stream);
+}
+
+int sfft4_execute_batched(sfft4_plan_t p, int32_t nsig, const void* x_dev, int64_t x_stride,
+                          int64_t* idx_dev, sfft4_c128* val_dev, int64_t* nfound_dev,
+                          int8_t* votes_dev, void* stream) {
+    if (!p || !x_dev || !idx_dev || !val_dev || !nfound_dev) return SFFT4_EINVAL;
+    if (nsig < 1 || nsig > p->o.max_batch || x_stride < p->N) return SFFT4_EINVAL;
+    return run(p, nsig, (const float2*)x_dev, x_stride, idx_dev, val_dev, nfound_dev, votes_dev,
+               (cudaStream_t)stream);
+}
+
+int sfft4_bucketize(sfft4_plan_t p, const void* x_dev, int32_t signal, int32_t m, void* y_dev,
+                    void* stream) {
+    if (!p || !x_dev || !y_dev || signal < 0 || m < 1 || m > (int32_t)p->iters.size())
+        return SFFT4_EINVAL;
+    const IterDev& d = p->iters[m - 1].d;
+    return launch_bucketize(p, m - 1, 1, (const float2*)x_dev, p->N, signal, (float2*)y_dev,
+                            (int64_t)d.R * d.B, (cudaStream_t)stream);
+}
+
+int sfft4_profile_get(sfft4_plan_t p, sfft4_profile* out, int32_t reset) {
+    if (!p || !out) return SFFT4_EINVAL;
+    if (!p->o.profile) return SFFT4_ESTATE;
+    for (auto& r : p->prof) {
+        int rc = check_cuda(cudaEventSynchronize(r.b));
+        if (rc) return rc;
+        float ms = 0.f;
+        rc = check_cuda(cudaEventElapsedTime(&ms, r.a, r.b));
+        if (rc) return rc;
+        switch (r.kind) {
+            case kProfFold: p->prof_tot.fold_launches++; p->prof_tot.fold_ms += ms;
+                            p->prof_tot.fold_samples += r.samples; break;
+            case kProfFft: p->prof_tot.fft_launches++; p->prof_tot.fft_ms += ms; break;
+            case kProfDecode: p->prof_tot.decode_launches++; p->prof_tot.decode_ms += ms; break;
+            default: p->prof_tot.finalize_launches++; p->prof_tot.finalize_ms += ms; break;
+        }
+    }
+    p->prof.clear();
+    p->ev_used = 0;
+    *out = p->prof_tot;
+    if (reset) p->prof_tot = sfft4_profile{};
+    return SFFT4_OK;
+}
+
+int sfft4_trace_get(sfft4_plan_t p, int32_t m, void* y_host, int64_t cap, int64_t* f_host,
+                    sfft4_c128* v_host, int8_t* votes_host, int64_t* nfound) {
+    if (!p || m < 1 || m > (int32_t)p->iters.size()) return SFFT4_EINVAL;
+    if (!p->o.trace || !p->executed) return SFFT4_ESTATE;
+    int rc = check_cuda(cudaDeviceSynchronize());
+    if (rc) return rc;
+    const IterDev& d = p->iters[m - 1].d;
+    const int64_t rb = (int64_t)p->R_max * p->B_max;
+    if (y_host) {
+        rc = check_cuda(cudaMemcpy(y_host, p->trace_y + (m - 1) * rb, (size_t)d.R * d.B * sizeof(float2),
+                                   cudaMemcpyDeviceToHost));
+        if (rc) return rc;
+    }
+    int32_t F = 0;
+    rc = check_cuda(cudaMemcpy(&F, p->trace_F + (m - 1), sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (rc) return rc;
+    if (nfound) *nfound = F;
+    int64_t nc = std::min<int64_t>(F, cap);
+    if (nc > 0) {
+        std::vector<int32_t> f32(nc);
+        std::vector<double2> v(nc);
+        std::vector<int8_t> vt(nc);
+        rc = check_cuda(cudaMemcpy(f32.data(), p->trace_ff + (m - 1) * p->Fcap, nc * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if (!rc) rc = check_cuda(cudaMemcpy(v.data(), p->trace_fv + (m - 1) * p->Fcap, nc * sizeof(double2), cudaMemcpyDeviceToHost));
+        if (!rc) rc = check_cuda(cudaMemcpy(vt.data(), p->trace_votes + (m - 1) * p->Fcap, nc, cudaMemcpyDeviceToHost));
+        if (rc) return rc;
+        for (int64_t i = 0; i < nc; ++i) {
+            if (f_host) f_host[i] = f32[i];
+            if (v_host) { v_host[i].re = v[i].x; v_host[i].im = v[i].y; }
+            if (votes_host) votes_host[i] = vt[i];
+        }
+    }
+    return SFFT4_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,400 @@
+// Host planner of the sFFT4.0 library: validates parameters, builds the static schedule
+// of iterations (Section 3.1, Lemma 2), the multiscale levels and offsets of each iteration
+// (Section 3.2, Fig. 4), the fold segments, and allocates device tables and workspace.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "sfft4_internal.cuh"
+
+using namespace sfft4;
+
+namespace {
+
+thread_local char g_cuda_err[256] = "no error";
+
+int64_t pow2ceil(int64_t v) {
+    int64_t p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+int ilog2(int64_t v) {
+    int r = 0;
+    while ((int64_t(1) << r) < v) ++r;
+    return r;
+}
+
+// Inverse complementary error function by Newton's method on erfc (0 < y < 1).
+double erfcinv_newton(double y) {
+    // start from the asymptotic form erfc(x) ~ exp(-x^2) / (x sqrt(pi)) for small y
+    double x = (y < 0.5) ? sqrt(-log(y)) : 0.0;
+    if (y >= 0.5) x = (1.0 - y) * 0.886226925452758;  // erfinv(z) ~ sqrt(pi)/2 z
+    for (int i = 0; i < 100; ++i) {
+        double f = erfc(x) - y;
+        double d = -2.0 / sqrt(M_PI) * exp(-x * x);
+        double step = f / d;
+        x -= step;
+        if (fabs(step) <= 1e-17 * fabs(x)) break;
+    }
+    return x;
+}
+
+// Window half-width: frequency box of half-width 3L/4 convolved with a Gaussian of std
+// s_f = L / (4 sqrt 2 erfcinv(delta)); in time a Gaussian of std s_t = N / (2 pi s_f),
+// truncated at delta: h = ceil(s_t sqrt(2 ln(1/delta))) (flat window of Eq. 9).
+int64_t window_halfwidth(int64_t B, double delta, double* s_t_out) {
+    double c = 4.0 * sqrt(2.0) * erfcinv_newton(delta);
+    double s_t = (double)B * c / (2.0 * M_PI);
+    if (s_t_out) *s_t_out = s_t;
+    return (int64_t)ceil(s_t * sqrt(2.0 * log(1.0 / delta)));
+}
+
+// Nominal level lengths of a region of length L0 (Section 3.2): Lbar_{s+1} =
+// ceil((q+1) Lbar_s / l) + 1 while Lbar_s > l and the length still shrinks.
+std::vector<int64_t> levels(int64_t L0, int l, int qn) {
+    std::vector<int64_t> out{L0};
+    while (out.back() > l) {
+        int64_t num = (int64_t)(kQDen + qn) * out.back();
+        int64_t den = (int64_t)l * kQDen;
+        int64_t nxt = (num + den - 1) / den + 1;
+        if (nxt >= out.back()) break;
+        out.push_back(nxt);
+    }
+    return out;
+}
+
+// Static schedule (B_m, K_m): K_1 = K, B_m = clamp(pow2ceil(ceil(beta K_m)), 16, B_1),
+// K_{m+1} = K_m (1 - exp(-2 K_m / B_m)) until K_m < 1/2, then two more iterations.
+std::vector<std::pair<int64_t, double>> schedule(int64_t K, int64_t B1, int max_iters) {
+    std::vector<std::pair<int64_t, double>> out;
+    double beta = (double)B1 / (double)K;
+    double rem = (double)K;
+    while ((int)out.size() < max_iters) {
+        int64_t B = pow2ceil((int64_t)ceil(beta * rem));
+        B = std::max<int64_t>(kBMin, std::min<int64_t>(B1, B));
+        out.push_back({B, rem});
+        rem = rem * (1.0 - exp(-2.0 * rem / (double)B));
+        if (rem < 0.5) break;
+    }
+    for (int i = 0; i < 2; ++i)
+        if ((int)out.size() < max_iters) out.push_back({out.back().first, rem});
+    return out;
+}
+
+// Segments of the union of windows [tau_s - h, tau_s + h], s in [r0, r0 + nr).
+void build_group(FoldGroup* g, const int64_t* tau, int r0, int nr, int64_t h) {
+    g->r0 = r0;
+    g->nr = nr;
+    std::vector<std::pair<int64_t, int>> ev;  // (position, +/-(s+1))
+    for (int s = r0; s < r0 + nr; ++s) {
+        ev.push_back({tau[s] - h, s - r0 + 1});
+        ev.push_back({tau[s] + h + 1, -(s - r0 + 1)});
+    }
+    std::sort(ev.begin(), ev.end());
+    uint32_t mask = 0;
+    g->nseg = 0;
+    g->unique = 0;
+    for (size_t i = 0; i < ev.size(); ++i) {
+        int e = ev[i].second;
+        if (e > 0) mask |= 1u << (e - 1);
+        else mask &= ~(1u << (-e - 1));
+        if (i + 1 < ev.size() && ev[i + 1].first > ev[i].first && mask) {
+            g->t0[g->nseg] = ev[i].first;
+            g->t1[g->nseg] = ev[i + 1].first;
+            g->mask[g->nseg] = mask;
+            g->unique += ev[i + 1].first - ev[i].first;
+            g->nseg++;
+        }
+    }
+}
+
+void free_plan(sfft4_plan_s* p) {
+    if (!p) return;
+    for (auto& w : p->wins) {
+        cudaFree(w.G);
+        cudaFree(w.Ghat);
+        cudaFree(w.tw);
+    }
+    void* bufs[] = {p->iters_dev, p->z, p->y, p->F, p->ff, p->fv, p->fvotes, p->hkeys,
+                    p->hvals, p->theta, p->fxexp, p->trace_y, p->trace_F, p->trace_ff,
+                    p->trace_fv, p->trace_votes};
+    for (void* b : bufs) cudaFree(b);
+    for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    delete p;
+}
+
+}  // namespace
+
+namespace sfft4 {
+int check_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return SFFT4_OK;
+    snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? SFFT4_ENOMEM : SFFT4_ECUDA;
+}
+}  // namespace sfft4
+
+#define CK(call)                                   \
+    do {                                           \
+        int _rc = sfft4::check_cuda(call);         \
+        if (_rc != SFFT4_OK) { free_plan(p); return _rc; } \
+    } while (0)
+
+extern "C" {
+
+int sfft4_opts_default(sfft4_opts* o) {
+    if (!o) return SFFT4_EINVAL;
+    memset(o, 0, sizeof(*o));
+    o->delta = 1e-8;
+    o->precision = SFFT4_FP32;
+    o->select_factor = 2.0;
+    o->sig_floor = 1e-10;
+    o->mag_tol = 0.5;
+    o->max_iters = 64;
+    o->max_batch = 1;
+    return SFFT4_OK;
+}
+
+int sfft4_plan(sfft4_plan_t* out, int64_t N, int64_t K, int32_t l, double q, uint64_t seed,
+               const sfft4_opts* opts) {
+    if (!out) return SFFT4_EINVAL;
+    *out = nullptr;
+    sfft4_opts o;
+    sfft4_opts_default(&o);
+    if (opts) {
+        o = *opts;
+        if (o.delta == 0) o.delta = 1e-8;
+        if (o.select_factor == 0) o.select_factor = 2.0;
+        if (o.sig_floor == 0) o.sig_floor = 1e-10;
+        if (o.mag_tol == 0) o.mag_tol = 0.5;
+        if (o.max_iters == 0) o.max_iters = 64;
+        if (o.max_batch == 0) o.max_batch = 1;
+    }
+    if (N < 256 || (N & (N - 1)) || N > (int64_t(1) << 30)) return SFFT4_EINVAL;
+    if (K < 1 || K > N / 64 || K > kKMax) return SFFT4_EINVAL;
+    int qn = (int)floor(q * kQDen + 0.5);
+    if (!(q >= 0) || l < 2 || l > 32 || (int64_t)l * kQDen <= kQDen + qn) return SFFT4_EINVAL;
+    if (!(o.delta > 0 && o.delta < 0.5)) return SFFT4_EINVAL;
+    if (o.precision != SFFT4_FP32 && o.precision != SFFT4_BF16X3) return SFFT4_EINVAL;
+    if (o.max_batch < 1 || o.max_iters < 1 || o.max_iters > 256) return SFFT4_EINVAL;
+    if (!(o.select_factor > 0) || !(o.mag_tol > 0) || o.min_votes < 0) return SFFT4_EINVAL;
+    int64_t B1 = o.B1;
+    if (B1 == 0) B1 = std::max<int64_t>(kBMin, std::min<int64_t>({(int64_t)kBMax, N / 64, pow2ceil(2 * K)}));
+    if (B1 < kBMin || (B1 & (B1 - 1)) || B1 > N / 64 || B1 > kBMax) return SFFT4_EINVAL;
+
+    sfft4_plan_s* p = new (std::nothrow) sfft4_plan_s();
+    if (!p) return SFFT4_ENOMEM;
+    p->N = N;
+    p->n = ilog2(N);
+    p->K = K;
+    p->l = l;
+    p->qn = qn;
+    p->seed = seed;
+    p->o = o;
+    p->o.B1 = (int32_t)B1;
+    CK(cudaGetDevice(&p->device));
+
+    auto sch = schedule(K, B1, o.max_iters);
+    p->Fcap = 0;
+    for (size_t i = 0; i < sch.size(); ++i) {
+        int64_t B = sch[i].first;
+        IterHost ih;
+        memset(&ih.d, 0, sizeof(ih.d));
+        IterDev& d = ih.d;
+        d.m = (int32_t)i + 1;
+        d.B = (int32_t)B;
+        d.logB = ilog2(B);
+        d.L = N / B;
+        d.logL = ilog2(d.L);
+        d.n_c = (int32_t)std::min<int64_t>(B, (int64_t)ceil(o.select_factor * std::max(sch[i].second, 1.0)));
+        d.h = (int32_t)window_halfwidth(B, o.delta, nullptr);
+        if (2 * (int64_t)d.h + 1 > N / 2) { free_plan(p); return SFFT4_EINVAL; }
+        // search region [bL - L, bL + L): pass band plus the transition bands (reading R5')
+        std::vector<int64_t> lv = levels(2 * d.L, l, qn);
+        int S = (int)lv.size();
+        if (S + 1 > kMaxRounds) { free_plan(p); return SFFT4_EINVAL; }
+        d.S = S;
+        d.R = S + 1;
+        d.tau[0] = 0;
+        for (int s = 0; s < S; ++s) {
+            int64_t Lb = lv[s];
+            d.Lbar[s] = Lb;
+            int64_t ts;
+            if (s < S - 1) {
+                int64_t ext = ((int64_t)qn * Lb + (int64_t)l * kQDen - 1) / ((int64_t)l * kQDen);
+                ts = N / (Lb + ext);
+                d.H[s] = (uint32_t)((((int64_t)(kQDen + qn) * Lb * ts) << (32 - p->n)) /
+                                    (2 * (int64_t)l * kQDen));
+                d.W[s] = (uint64_t)(Lb * ts) << (32 - p->n);
+            } else {
+                ts = N / Lb;
+                d.H[s] = (uint32_t)((ts << (32 - p->n)) / 2);
+                d.W[s] = (uint64_t)ts << (32 - p->n);
+            }
+            d.tau[s + 1] = ts;
+        }
+        // fold groups of up to kFoldRG rounds
+        ih.Wj = (int32_t)std::min<int64_t>(B, 256);
+        ih.unique = 0;
+        for (int r0 = 0; r0 < d.R; r0 += kFoldRG) {
+            FoldGroup g;
+            build_group(&g, d.tau, r0, std::min(kFoldRG, d.R - r0), d.h);
+            int64_t per = g.unique / (B * 32);
+            g.P = (int32_t)std::max<int64_t>(1, std::min<int64_t>(512 / ih.Wj, per));
+            ih.groups.push_back(g);
+        }
+        {
+            FoldGroup all;
+            // the union over all rounds (for the sample count) -- at most 2R segments
+            std::vector<std::pair<int64_t, int64_t>> iv;
+            for (int s = 0; s <= S; ++s) iv.push_back({d.tau[s] - d.h, d.tau[s] + d.h});
+            std::sort(iv.begin(), iv.end());
+            int64_t lo = iv[0].first, hi = iv[0].second, tot = 0;
+            for (size_t k = 1; k < iv.size(); ++k) {
+                if (iv[k].first > hi + 1) { tot += hi - lo + 1; lo = iv[k].first; hi = iv[k].second; }
+                else hi = std::max(hi, iv[k].second);
+            }
+            tot += hi - lo + 1;
+            ih.unique = std::min(tot, N);
+            (void)all;
+        }
+        p->samples += ih.unique;
+        // window of this bucket count
+        int wi = -1;
+        for (size_t k = 0; k < p->wins.size(); ++k)
+            if (p->wins[k].B == B) wi = (int)k;
+        if (wi < 0) {
+            Window w;
+            w.B = (int32_t)B;
+            w.h = d.h;
+            w.L = d.L;
+            p->wins.push_back(w);
+            wi = (int)p->wins.size() - 1;
+        }
+        ih.win = wi;
+        p->Fcap += d.n_c;
+        p->B_max = std::max<int32_t>(p->B_max, (int32_t)B);
+        p->R_max = std::max<int32_t>(p->R_max, d.R);
+        p->iters.push_back(ih);
+    }
+    p->Hlog = ilog2(2 * p->Fcap + 2);
+
+    for (auto& w : p->wins) {
+        int rc = build_window_tables(p, &w, o.delta);
+        if (rc != SFFT4_OK) { free_plan(p); return rc; }
+    }
+    for (auto& ih : p->iters) {
+        const Window& w = p->wins[ih.win];
+        ih.d.G = w.G;
+        ih.d.Ghat = w.Ghat;
+        ih.d.tw = w.tw;
+    }
+    size_t ni = p->iters.size();
+    CK(cudaMalloc(&p->iters_dev, ni * sizeof(IterDev)));
+    std::vector<IterDev> hd(ni);
+    for (size_t i = 0; i < ni; ++i) hd[i] = p->iters[i].d;
+    CK(cudaMemcpy(p->iters_dev, hd.data(), ni * sizeof(IterDev), cudaMemcpyHostToDevice));
+
+    size_t mb = (size_t)o.max_batch;
+    size_t rb = (size_t)p->R_max * p->B_max;
+    CK(cudaMalloc(&p->z, mb * rb * sizeof(float2)));
+    CK(cudaMalloc(&p->y, mb * rb * sizeof(float2)));
+    CK(cudaMalloc(&p->F, mb * sizeof(int32_t)));
+    CK(cudaMalloc(&p->ff, mb * p->Fcap * sizeof(int32_t)));
+    CK(cudaMalloc(&p->fv, mb * p->Fcap * sizeof(double2)));
+    CK(cudaMalloc(&p->fvotes, mb * p->Fcap * sizeof(int8_t)));
+    CK(cudaMalloc(&p->hkeys, mb * ((size_t)1 << p->Hlog) * sizeof(int32_t)));
+    CK(cudaMalloc(&p->hvals, mb * ((size_t)1 << p->Hlog) * sizeof(int32_t)));
+    CK(cudaMalloc(&p->theta, mb * sizeof(float)));
+    CK(cudaMalloc(&p->fxexp, mb * sizeof(int32_t)));
+    if (o.trace) {
+        CK(cudaMalloc(&p->trace_y, ni * rb * sizeof(float2)));
+        CK(cudaMalloc(&p->trace_F, ni * sizeof(int32_t)));
+        CK(cudaMalloc(&p->trace_ff, ni * p->Fcap * sizeof(int32_t)));
+        CK(cudaMalloc(&p->trace_fv, ni * p->Fcap * sizeof(double2)));
+        CK(cudaMalloc(&p->trace_votes, ni * p->Fcap * sizeof(int8_t)));
+    }
+    CK(cudaDeviceSynchronize());
+    *out = p;
+    return SFFT4_OK;
+}
+
+void sfft4_destroy(sfft4_plan_t p) {
+    if (!p) return;
+    cudaDeviceSynchronize();
+    free_plan(p);
+}
+
+int sfft4_get_plan_info(sfft4_plan_t p, sfft4_plan_info* info) {
+    if (!p || !info) return SFFT4_EINVAL;
+    memset(info, 0, sizeof(*info));
+    info->N = p->N;
+    info->K = p->K;
+    info->l = p->l;
+    info->q_num = p->qn;
+    info->B1 = p->o.B1;
+    info->n_iters = (int32_t)p->iters.size();
+    info->max_R = p->R_max;
+    info->precision = p->o.precision;
+    info->samples_per_transform = p->samples;
+    info->found_capacity = p->Fcap;
+    int32_t kpe = 1;
+    for (auto& ih : p->iters) kpe += (int32_t)ih.groups.size() + 2;
+    info->kernels_per_execute = kpe;
+    return SFFT4_OK;
+}
+
+int sfft4_get_iter_info(sfft4_plan_t p, int32_t m, sfft4_iter_info* info) {
+    if (!p || !info || m < 1 || m > (int32_t)p->iters.size()) return SFFT4_EINVAL;
+    const IterHost& ih = p->iters[m - 1];
+    memset(info, 0, sizeof(*info));
+    info->B = ih.d.B;
+    info->S = ih.d.S;
+    info->n_c = ih.d.n_c;
+    info->h = ih.d.h;
+    info->L = ih.d.L;
+    for (int s = 0; s < ih.d.S; ++s) {
+        info->Lbar[s] = ih.d.Lbar[s];
+        info->H[s] = ih.d.H[s];
+    }
+    for (int s = 0; s <= ih.d.S; ++s) info->tau[s] = ih.d.tau[s];
+    info->unique_samples = ih.unique;
+    return SFFT4_OK;
+}
+
+int sfft4_get_window(sfft4_plan_t p, int32_t B, float* G_host, float* Ghat_host) {
+    if (!p) return SFFT4_EINVAL;
+    for (auto& w : p->wins) {
+        if (w.B != B) continue;
+        if (G_host) {
+            int rc = check_cuda(cudaMemcpy(G_host, w.G, (2 * (size_t)w.h + 1) * sizeof(float),
+                                           cudaMemcpyDeviceToHost));
+            if (rc) return rc;
+        }
+        if (Ghat_host) {
+            int rc = check_cuda(cudaMemcpy(Ghat_host, w.Ghat, (3 * (size_t)w.L / 2 + 1) * sizeof(float),
+                                           cudaMemcpyDeviceToHost));
+            if (rc) return rc;
+        }
+        return SFFT4_OK;
+    }
+    return SFFT4_EINVAL;
+}
+
+const char* sfft4_strerror(int code) {
+    switch (code) {
+        case SFFT4_OK: return "ok";
+        case SFFT4_EINVAL: return "invalid argument";
+        case SFFT4_ENOMEM: return "out of memory";
+        case SFFT4_ECUDA: return "CUDA error";
+        case SFFT4_ESTATE: return "invalid plan state";
+        default: return "unknown error";
+    }
+}
+
+const char* sfft4_last_cuda_error(void) { return g_cuda_err; }
+
+}  // extern "C"

@@ -1,0 +1,180 @@
+// Internal definitions of the sFFT4.0 GB300 library: plan structures shared by the host
+// planner and the kernels, and small device helpers (Philox, modular inverse, fixed-point
+// phases).  Nothing here is part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "sfft4.h"
+
+namespace sfft4 {
+
+constexpr int kMaxRounds = SFFT4_MAX_ROUNDS;  // R = S + 1 <= 64 rounds per iteration
+constexpr int kFoldRG = 8;                    // rounds accumulated per fold launch group
+constexpr int kMaxSeg = 2 * kFoldRG + 2;      // t-segments of one fold group
+constexpr int kQDen = 256;                    // q = q_n / 256
+constexpr int kBMin = 16;
+constexpr int kBMax = 4096;
+constexpr int kKMax = 4096;
+constexpr int kDecodeThreads = 1024;
+
+// Rounds [r0, r0 + nr) of one iteration that one fold launch accumulates, and the
+// t-segments covering the union of their windows [tau_s - h, tau_s + h]; within a segment
+// the set of covering rounds (mask, bit s - r0) is constant.
+struct FoldGroup {
+    int32_t r0, nr, nseg;
+    int32_t P;                 // copies per residue (threads per slot)
+    int64_t t0[kMaxSeg], t1[kMaxSeg];  // half-open [t0, t1)
+    uint32_t mask[kMaxSeg];
+    int64_t unique;            // samples this group reads
+};
+
+// Device-resident parameters of one iteration (read by the fold, FFT and decode kernels).
+struct IterDev {
+    int32_t m, B, logB, S, R, n_c, h, logL;
+    int64_t L;
+    int64_t Lbar[kMaxRounds];          // levels 1..S at index 0..S-1
+    int64_t tau[kMaxRounds + 1];       // tau_0 = 0 .. tau_S
+    uint32_t H[kMaxRounds];            // vote thresholds, levels 1..S at index 0..S-1
+    uint64_t W[kMaxRounds];            // phase span (Lbar_s tau_s) << (32 - n) of level s
+    const float* G;                    // w = 2h + 1 window coefficients G_{-h..h}
+    const float* Ghat;                 // G'^_k for k = 0..3L/2
+    const float2* tw;                  // e^{-2 pi i k / B}, k < B/2
+};
+
+struct Window {
+    int32_t B, h;
+    int64_t L;
+    float* G = nullptr;        // device, 2h + 1
+    float* Ghat = nullptr;     // device, 3L/2 + 1
+    float2* tw = nullptr;      // device, B/2
+};
+
+struct IterHost {
+    IterDev d;
+    std::vector<FoldGroup> groups;
+    int64_t unique;            // |union_s [tau_s - h, tau_s + h]|
+    int32_t win;               // index into plan windows
+    int32_t Wj;                // residues per fold CTA
+};
+
+// ------------------------------------------------------------------ device helpers ---
+#define SFFT4_HD __host__ __device__ __forceinline__
+
+SFFT4_HD uint64_t mulhi64(uint64_t a, uint64_t b) {
+#ifdef __CUDA_ARCH__
+    return __umul64hi(a, b);
+#else
+    return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+// Philox4x64-10 (Salmon et al., SC'11): one 4 x 64-bit block for a counter and key.
+SFFT4_HD void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+    for (int r = 0; r < 10; ++r) {
+        uint64_t lo0 = M0 * c[0], hi0 = mulhi64(M0, c[0]);
+        uint64_t lo1 = M1 * c[2], hi1 = mulhi64(M1, c[2]);
+        uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+        k0 += W0; k1 += W1;
+    }
+}
+
+// (sigma, a) of iteration m of signal `signal`: counter (signal, m, 0, 0), key (seed, 0);
+// sigma = 2 (r0 mod N/2) + 1 is odd (invertible mod N = 2^n), a = r1 mod N (Section 2.2).
+SFFT4_HD void permutation_draw(uint64_t seed, uint64_t signal, uint64_t m, uint64_t N,
+                               uint64_t* sigma, uint64_t* a) {
+    uint64_t c[4] = {signal, m, 0, 0};
+    philox4x64_10(c, seed, 0);
+    *sigma = 2 * (c[0] & (N / 2 - 1)) + 1;
+    *a = c[1] & (N - 1);
+}
+
+// Inverse of an odd sigma modulo 2^64 by Newton's iteration x <- x (2 - sigma x).
+SFFT4_HD uint64_t inv_odd64(uint64_t s) {
+    uint64_t x = s;  // correct to 3 bits for odd s
+    for (int i = 0; i < 5; ++i) x *= 2 - s * x;
+    return x;
+}
+
+// Distance of two phases held as 2^-32 turns, on the circle.
+SFFT4_HD uint32_t circ_dist(uint32_t a, uint32_t b) {
+    uint32_t d = a - b;
+    uint32_t e = b - a;
+    return d < e ? d : e;
+}
+
+// floor(a / b) for b > 0 and any sign of a.
+SFFT4_HD int64_t floor_div(int64_t a, int64_t b) {
+    int64_t q = a / b;
+    if ((a % b != 0) && (a < 0)) --q;
+    return q;
+}
+
+}  // namespace sfft4
+
+// The opaque plan.
+struct sfft4_plan_s {
+    int64_t N;
+    int n;
+    int64_t K;
+    int32_t l, qn;
+    uint64_t seed;
+    sfft4_opts o;
+    int device;
+    std::vector<sfft4::IterHost> iters;
+    std::vector<sfft4::Window> wins;
+    sfft4::IterDev* iters_dev = nullptr;
+    int32_t B_max = 0, R_max = 0;
+    int64_t Fcap = 0;           // found entries per signal
+    int32_t Hlog = 0;           // log2 of hash slots per signal
+    int64_t samples = 0;        // distinct samples per transform
+    // workspace for o.max_batch signals
+    float2* z = nullptr;        // [sig][R_max][B_max] folded, before the DFT
+    float2* y = nullptr;        // [sig][R_max][B_max] bucket arrays
+    int32_t* F = nullptr;       // [sig] found count
+    int32_t* ff = nullptr;      // [sig][Fcap] frequency
+    double2* fv = nullptr;      // [sig][Fcap] value
+    int8_t* fvotes = nullptr;   // [sig][Fcap]
+    int32_t* hkeys = nullptr;   // [sig][2^Hlog] hash keys (frequency or -1)
+    int32_t* hvals = nullptr;   // [sig][2^Hlog] entry index
+    float* theta = nullptr;     // [sig] candidate floor
+    int32_t* fxexp = nullptr;   // [sig] fixed-point exponent of the bucket update
+    // trace of signal 0 (opts.trace)
+    float2* trace_y = nullptr;      // [iter][R_max][B_max]
+    int32_t* trace_F = nullptr;     // [iter]
+    int32_t* trace_ff = nullptr;    // [iter][Fcap]
+    double2* trace_fv = nullptr;    // [iter][Fcap]
+    int8_t* trace_votes = nullptr;  // [iter][Fcap]
+    bool executed = false;
+    // profiling (opts.profile): event pairs recorded around launches, by kind
+    struct Prof {
+        cudaEvent_t a, b;
+        int kind;
+        int64_t samples;
+    };
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<Prof> prof;
+    size_t ev_used = 0;
+    sfft4_profile prof_tot{};
+};
+
+namespace sfft4 {
+// Implemented in kernels.cu.
+int build_window_tables(sfft4_plan_s* p, Window* w, double delta);
+int launch_bucketize(sfft4_plan_s* p, int m_index, int nsig, const float2* x, int64_t x_stride,
+                     int32_t signal0, float2* y_out, int64_t y_sig_stride, cudaStream_t st);
+int launch_decode(sfft4_plan_s* p, int m_index, int nsig, cudaStream_t st);
+int launch_finalize(sfft4_plan_s* p, int nsig, int64_t* idx, sfft4_c128* val, int64_t* nfound,
+                    int8_t* votes, cudaStream_t st);
+int launch_reset(sfft4_plan_s* p, int nsig, cudaStream_t st);
+int prof_begin(sfft4_plan_s* p, cudaStream_t st, cudaEvent_t* a);
+int prof_end(sfft4_plan_s* p, cudaStream_t st, cudaEvent_t a, int kind, int64_t samples);
+enum { kProfFold = 0, kProfFft = 1, kProfDecode = 2, kProfFinalize = 3 };
+int check_cuda(cudaError_t e);
+}  // namespace sfft4
