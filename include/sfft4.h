@@ -68,6 +68,10 @@ typedef struct {
                                 of signal 0 for sfft4_trace_get (tests); default 0         */
     int32_t profile;         /* nonzero: bracket each kernel launch of an execute with CUDA
                                 events on the execution stream (sfft4_profile_get)        */
+    int32_t l2_fetch_bytes;  /* L2 fetch granularity hint the plan sets on the calling
+                                process's CUDA context (cudaLimitMaxL2FetchGranularity):
+                                0 = 32 bytes (one sector per gathered sample), negative =
+                                leave the context's limit unchanged                        */
 } sfft4_opts;
 
 /* Fills *opts with the defaults above.  Returns SFFT4_EINVAL if opts is NULL. */

@@ -21,7 +21,8 @@ class Opts(ctypes.Structure):
                 ("min_votes", ctypes.c_int32), ("select_factor", ctypes.c_double),
                 ("sig_floor", ctypes.c_double), ("mag_tol", ctypes.c_double),
                 ("max_iters", ctypes.c_int32), ("max_batch", ctypes.c_int32),
-                ("trace", ctypes.c_int32), ("profile", ctypes.c_int32)]
+                ("trace", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("l2_fetch_bytes", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):

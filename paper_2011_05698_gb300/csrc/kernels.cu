@@ -154,64 +154,80 @@ struct FoldArgs {
     float2* z;
     int64_t z_stride;
     uint64_t N, seed;
-    int32_t m, signal0, B, Wj, h;
+    int32_t m, signal0, B, logB, Wj, h, w, Mrows;
     const float* G;
     FoldGroup g;
-    int64_t tau[kFoldRG];
+    int32_t tau[kFoldRG];
+    int32_t mlo[kFoldRG];   // first multiple m' of B with rows of round s in shared memory
+    int32_t soff[kFoldRG];  // (s Mrows - mlo_s) Wj: shared-memory offset of round s
 };
 
-constexpr int kFoldUnroll = 8;
+constexpr int kFoldUnroll = 4;
 
-// One CTA = (signal, slice of Wj residues mod B); thread (jj, p) owns the samples
-// t = rho + k P B with rho = slice Wj + jj + p B, so its fold slot for round s,
+// One CTA = (signal, slice of Wj residues mod B).  Thread (jj, p) owns the samples
+// t = rho + m' B with rho = slice Wj + jj and m' = p (mod P), so its fold slot for round s,
 // (t - tau_s) mod B, is fixed: it accumulates in registers, then the P copies of each slot
 // are summed in a fixed order.  Each x sample is loaded once for all rounds whose window
-// covers it.
+// covers it.  The window coefficients the CTA needs, G[rho + m' B - tau_s + h], are staged
+// in shared memory at the start (rows m' of Wj contiguous coefficients, zero outside the
+// window), so the main loop issues only the random gathers of x.  Index arithmetic is exact
+// in 32 bits: N = 2^n divides 2^32, so (sigma t + a) mod N is the low n bits of the wrapped
+// 32-bit value.
 template <int RG>
-__global__ void __launch_bounds__(512) k_fold(const FoldArgs a) {
-    __shared__ uint64_t s_par[2];
+__global__ void __launch_bounds__(512, 2) k_fold(const FoldArgs a) {
+    extern __shared__ float gsm[];  // [RG][Mrows][Wj]
+    __shared__ uint32_t s_par[2];
     __shared__ float2 red[512];
-    const int tid = threadIdx.x;
-    const int Wj = a.Wj, B = a.B;
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int Wj = a.Wj, B = a.B, Mrows = a.Mrows;
     const int P = a.g.P;
     const int jj = tid % Wj, p = tid / Wj;
     const int sig = blockIdx.y;
+    const int rho0 = blockIdx.x * Wj;
     if (tid == 0) {
         uint64_t s, o;
         permutation_draw(a.seed, (uint64_t)(a.signal0 + sig), (uint64_t)a.m, a.N, &s, &o);
-        s_par[0] = s;
-        s_par[1] = o;
+        s_par[0] = (uint32_t)s;
+        s_par[1] = (uint32_t)o;
+    }
+    // stage the window rows of this residue slice
+    const float* __restrict__ G = a.G;
+    for (int i = tid; i < a.g.nr * Mrows * Wj; i += T) {
+        const int s = i / (Mrows * Wj);
+        const int rem = i - s * Mrows * Wj;
+        const int row = rem / Wj, c = rem - row * Wj;
+        const int gi = rho0 + c + (row + a.mlo[s]) * B - a.tau[s] + a.h;
+        gsm[i] = (gi >= 0 && gi < a.w) ? __ldg(G + gi) : 0.f;
     }
     __syncthreads();
-    const uint64_t sigma = s_par[0], aoff = s_par[1], mask = a.N - 1;
-    const int64_t PB = (int64_t)P * B;
-    const int64_t rho = (int64_t)blockIdx.x * Wj + jj + (int64_t)p * B;
-    const uint64_t step = (sigma * (uint64_t)PB) & mask;
+    const uint32_t sigma = s_par[0], aoff = s_par[1], mask = (uint32_t)(a.N - 1);
+    const int PB = P * B;
+    const int rho = rho0 + jj + p * B;  // residue mod P B
+    const uint32_t step = sigma * (uint32_t)PB;
     const float2* __restrict__ x = a.x + (int64_t)sig * a.x_stride;
-    const float* __restrict__ G = a.G;
     float2 acc[RG];
 #pragma unroll
     for (int s = 0; s < RG; ++s) acc[s] = make_float2(0.f, 0.f);
 
     for (int sg = 0; sg < a.g.nseg; ++sg) {
-        const int64_t t0 = a.g.t0[sg], t1 = a.g.t1[sg];
+        const int t0 = (int)a.g.t0[sg], t1 = (int)a.g.t1[sg];
         const uint32_t rm = a.g.mask[sg];
-        int64_t d = (rho - t0) % PB;
+        int d = (rho - t0) % PB;
         if (d < 0) d += PB;
-        const int64_t t = t0 + d;
+        const int t = t0 + d;
         if (t >= t1) continue;
-        const int cnt = (int)((t1 - t + PB - 1) / PB);
-        uint64_t idx = (sigma * (uint64_t)t + aoff) & mask;
-        int gb[RG];
-#pragma unroll
-        for (int s = 0; s < RG; ++s) gb[s] = (int)(t - a.tau[s] + a.h);
-        const int pbi = (int)PB;
+        const int cnt = (t1 - t + PB - 1) / PB;
+        uint32_t idx = sigma * (uint32_t)t + aoff;
+        // shared-memory row of sample k of round s: (t + k P B - rho0 - jj) / B - mlo_s
+        const int m0 = (t - rho0 - jj) >> a.logB;
+        const int rowbase = m0 * Wj + jj;
+        const int rowstep = P * Wj;
         for (int k = 0; k < cnt; k += kFoldUnroll) {
             float2 v[kFoldUnroll];
 #pragma unroll
             for (int u = 0; u < kFoldUnroll; ++u) {
-                v[u] = (k + u < cnt) ? ld_stream(x + idx) : make_float2(0.f, 0.f);
-                idx = (idx + step) & mask;
+                v[u] = (k + u < cnt) ? ld_stream(x + (idx & mask)) : make_float2(0.f, 0.f);
+                idx += step;
             }
 #pragma unroll
             for (int u = 0; u < kFoldUnroll; ++u) {
@@ -219,7 +235,7 @@ __global__ void __launch_bounds__(512) k_fold(const FoldArgs a) {
 #pragma unroll
                     for (int s = 0; s < RG; ++s) {
                         if ((rm >> s) & 1u) {
-                            const float gw = __ldg(G + gb[s] + (k + u) * pbi);
+                            const float gw = gsm[a.soff[s] + rowbase + (k + u) * rowstep];
                             acc[s].x = fmaf(gw, v[u].x, acc[s].x);
                             acc[s].y = fmaf(gw, v[u].y, acc[s].y);
                         }
@@ -240,7 +256,7 @@ __global__ void __launch_bounds__(512) k_fold(const FoldArgs a) {
                     sum.x += o.x;
                     sum.y += o.y;
                 }
-                int64_t slot = ((int64_t)blockIdx.x * Wj + jj - a.tau[s]) % B;
+                int slot = (rho0 + jj - a.tau[s]) % B;
                 if (slot < 0) slot += B;
                 a.z[(int64_t)sig * a.z_stride + (int64_t)(a.g.r0 + s) * B + slot] = sum;
             }
@@ -360,6 +376,14 @@ __device__ void hash_insert(int32_t* keys, int32_t* vals, int Hlog, int32_t f, i
 }
 
 // ----------------------------------------------------------------- decode -----------
+// Dynamic shared memory of k_decode for B buckets: 26 B bytes of per-bucket arrays, and
+// at least 64 KB for the update's accumulators.
+__host__ __device__ inline size_t decode_smem(int B) {
+    const size_t base = 26 * (size_t)B;
+    const size_t upd = 64 * 1024;  // update accumulators (all rounds at once for small B)
+    return base > upd ? base : upd;
+}
+
 struct DecodeArgs {
     uint64_t N, seed;
     int32_t n, signal0, first, l, qn, min_votes;
@@ -379,25 +403,128 @@ struct DecodeArgs {
     int32_t* fxexp;
 };
 
-__device__ __forceinline__ float med_sorted(float* v, int R) {
-    for (int i = 1; i < R; ++i) {
-        float x = v[i];
-        int j = i - 1;
-        while (j >= 0 && v[j] > x) {
-            v[j + 1] = v[j];
-            --j;
+// Median of v[0..R-1] (R <= RMAX): mean of the two middle values for even R (Eq. 14
+// over rounds, reading R12).  RMAX = 16 sorts a fully unrolled bitonic network in registers
+// (entries r >= R padded with +inf); larger RMAX falls back to an insertion sort.
+template <int RMAX>
+__device__ __forceinline__ float median_of(float (&v)[RMAX], int R) {
+    if (RMAX <= 16) {
+#pragma unroll
+        for (int i = 0; i < RMAX; ++i)
+            if (i >= R) v[i] = __int_as_float(0x7f800000);
+#pragma unroll
+        for (int k = 2; k <= RMAX; k <<= 1) {
+#pragma unroll
+            for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+                for (int i = 0; i < RMAX; ++i) {
+                    const int ixj = i ^ j;
+                    if (ixj > i) {
+                        const float lo = fminf(v[i], v[ixj]), hi = fmaxf(v[i], v[ixj]);
+                        const bool up = (i & k) == 0;
+                        v[i] = up ? lo : hi;
+                        v[ixj] = up ? hi : lo;
+                    }
+                }
+            }
         }
-        v[j + 1] = x;
+    } else {
+        for (int i = 1; i < R; ++i) {
+            float x = v[i];
+            int j = i - 1;
+            while (j >= 0 && v[j] > x) {
+                v[j + 1] = v[j];
+                --j;
+            }
+            v[j + 1] = x;
+        }
     }
-    return (R & 1) ? v[R / 2] : 0.5f * (v[R / 2 - 1] + v[R / 2]);
+    float lo = 0.f, hi = 0.f;
+#pragma unroll
+    for (int i = 0; i < RMAX; ++i) {
+        if (i == (R - 1) / 2) lo = v[i];
+        if (i == R / 2) hi = v[i];
+    }
+    return (R & 1) ? hi : 0.5f * (lo + hi);
+}
+
+__device__ __forceinline__ uint32_t phase_fixed(float2 ys, float2 y0) {
+    const float cr = ys.x * y0.x + ys.y * y0.y;
+    const float cim = ys.y * y0.x - ys.x * y0.y;
+    const float turns = atan2f(cim, cr) * 0.15915494309189535f;
+    return (uint32_t)__float2ll_rn(turns * 4294967296.0f);
+}
+
+// Radix select over 32-bit keys held one chunk per thread: returns the value T of the
+// n-th largest key (1 <= n <= count) by four passes over 8-bit digits, most significant
+// first.  hist must hold 256 ints of shared memory; all threads of the block call it.
+__device__ uint32_t block_radix_select(const float* key, int b_lo, int b_hi, int n, int* hist,
+                                       int* s_bcast) {
+    uint32_t prefix = 0, pmask = 0;
+    int rank = n;  // rank of the wanted key among keys matching the prefix (1 = largest)
+    for (int d = 3; d >= 0; --d) {
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+        __syncthreads();
+        // warp-aggregated: lanes holding the same digit add once (keys cluster in a few
+        // exponent bins, so plain atomics would serialise on those bins)
+        constexpr int kChunkMax = (kBMax + kDecodeThreads - 1) / kDecodeThreads;
+        for (int e = 0; e < kChunkMax; ++e) {
+            const int b = b_lo + e;
+            int digit = 256;
+            if (b < b_hi) {
+                const uint32_t k = __float_as_uint(key[b]);
+                if ((k & pmask) == prefix) digit = (int)((k >> (8 * d)) & 255u);
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, digit);
+            if (digit < 256 && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1))
+                atomicAdd(&hist[digit], __popc(peers));
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            // suffix sums from the top digit down: lane owns digits [248 - 8 lane, 255 - 8 lane]
+            const int lane = threadIdx.x;
+            int loc[8], tot = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) { loc[q] = hist[255 - 8 * lane - q]; tot += loc[q]; }
+            int incl = tot;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            int before = incl - tot;  // keys with a larger digit than this lane's range
+            if (before < rank && rank <= incl) {
+                int c = before;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (c < rank && rank <= c + loc[q]) {
+                        s_bcast[0] = 255 - 8 * lane - q;
+                        s_bcast[1] = rank - c;
+                    }
+                    c += loc[q];
+                }
+            }
+        }
+        __syncthreads();
+        prefix |= (uint32_t)s_bcast[0] << (8 * d);
+        pmask |= 255u << (8 * d);
+        rank = s_bcast[1];
+        __syncthreads();
+    }
+    return prefix;
 }
 
 // One CTA per signal: update the bucket arrays by the found set, select the large
 // buckets, locate each candidate by the multiscale method, vote, estimate and merge.
+// All modular arithmetic is exact in 32 bits (N = 2^n divides 2^32).  RMAX bounds the
+// rounds R of the iteration (16, or 64 for extreme (l, q)).
+template <int RMAX>
 __global__ void __launch_bounds__(kDecodeThreads) k_decode(const DecodeArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ uint64_t s_par[3];
+    __shared__ uint32_t s_par[3];
     __shared__ int s_ws[33];
+    __shared__ int s_hist[256];
+    __shared__ int s_bc[2];
     __shared__ int s_cnt;
     __shared__ unsigned s_max;
     __shared__ float s_theta;
@@ -406,8 +533,8 @@ __global__ void __launch_bounds__(kDecodeThreads) k_decode(const DecodeArgs a) {
     const int tid = threadIdx.x, T = blockDim.x;
     const int sig = blockIdx.x;
     const int B = it->B, R = it->R, S = it->S, logL = it->logL;
-    const int64_t L = it->L;
-    const uint64_t N = a.N, mask = N - 1;
+    const uint32_t L = (uint32_t)it->L;
+    const uint32_t N = (uint32_t)a.N, mask = N - 1, halfN = N >> 1;
     const int n = a.n, shift = 32 - n;
     float2* Y = a.y + (int64_t)sig * a.y_stride;
     int32_t* ff = a.ff + (int64_t)sig * a.Fcap;
@@ -417,16 +544,16 @@ __global__ void __launch_bounds__(kDecodeThreads) k_decode(const DecodeArgs a) {
     int32_t* hv = a.hvals + ((int64_t)sig << a.Hlog);
     if (tid == 0) {
         uint64_t s, o;
-        permutation_draw(a.seed, (uint64_t)(a.signal0 + sig), (uint64_t)it->m, N, &s, &o);
-        s_par[0] = s;
-        s_par[1] = o;
-        s_par[2] = inv_odd64(s) & mask;
+        permutation_draw(a.seed, (uint64_t)(a.signal0 + sig), (uint64_t)it->m, a.N, &s, &o);
+        s_par[0] = (uint32_t)s;
+        s_par[1] = (uint32_t)o;
+        s_par[2] = (uint32_t)inv_odd64(s) & (uint32_t)(a.N - 1);
         s_cnt = 0;
         s_max = 0;
         s_fx = a.first ? 0 : a.fxexp[sig];
     }
     __syncthreads();
-    const uint64_t sigma = s_par[0], aoff = s_par[1], sinv = s_par[2];
+    const uint32_t sigma = s_par[0], aoff = s_par[1], sinv = s_par[2];
     const int F0 = a.F[sig];
 
     // shared memory (bytes, 26 B in total): [0, 16B) the update's int64 accumulators, later
@@ -440,41 +567,68 @@ __global__ void __launch_bounds__(kDecodeThreads) k_decode(const DecodeArgs a) {
     uint16_t* cand = (uint16_t*)(smraw + 20 * (size_t)B);
     int32_t* cexist = (int32_t*)(smraw + 22 * (size_t)B);
 
-    // ---- 1. update: yhat' = yhat - yhat_update, round by round (Section 3.1) ----------
-    // Contributions of the found coefficients are accumulated in int64 fixed point
-    // (2^(fx-40) units, fx = exponent of the largest bucket of iteration 1) with integer
-    // atomics, so the result does not depend on the order of the additions.
+    // ---- 1. update: yhat' = yhat - yhat_update (Section 3.1, iteration steps 2-3) ------
+    // Each found (f, v) adds G'^_{b'L-u} v e^{2 pi i f o_r / N} to buckets b' = b(u)-1..b(u)+1
+    // of every round r.  Contributions accumulate in int64 fixed point (2^(fx-40) units,
+    // fx = exponent of the largest bucket of iteration 1) with integer atomics, so the sum
+    // does not depend on the order of the additions.  Rounds are processed in passes of
+    // `rc` rounds with `nco` warp-private copies of the accumulators (many entries share few
+    // buckets when B is small); per-entry invariants are computed once.
     if (!a.first && F0 > 0) {
         const int fx = s_fx;
         const float scale = ldexpf(1.f, 40 - fx);
         const float iscale = ldexpf(1.f, fx - 40);
-        for (int r = 0; r < R; ++r) {
-            for (int i = tid; i < 2 * B; i += T) acc[i] = 0;
+        const size_t budget = decode_smem(B) / sizeof(long long);  // int64 slots available
+        const int per_round = 2 * B;
+        int rc = (int)((size_t)R < budget / per_round ? (size_t)R : budget / per_round);
+        if (rc < 1) rc = 1;
+        const size_t ncmax = budget / ((size_t)rc * per_round);
+        int nco = (int)((size_t)(T >> 5) < ncmax ? (size_t)(T >> 5) : ncmax);
+        if (nco < 1) nco = 1;
+        long long* wacc = acc + (size_t)((tid >> 5) % nco) * rc * per_round;
+        for (int r0 = 0; r0 < R; r0 += rc) {
+            const int nr = min(rc, R - r0);
+            for (int i = tid; i < nco * rc * per_round; i += T) acc[i] = 0;
             __syncthreads();
-            const uint64_t o_r = (aoff + sigma * (uint64_t)it->tau[r]) & mask;
             for (int i = tid; i < F0; i += T) {
-                const uint64_t f = (uint64_t)ff[i];
+                const uint32_t f = (uint32_t)ff[i];
                 const double2 vd = fv[i];
                 const float2 v = make_float2((float)vd.x, (float)vd.y);
-                const uint64_t u = (sigma * f) & mask;
-                const int b0 = (int)(((u + (uint64_t)(L >> 1)) >> logL) & (uint64_t)(B - 1));
-                const float2 c = cmul(v, cis_2pi_frac((f * o_r) & mask, n));
+                const uint32_t u = (sigma * f) & mask;
+                const int b0 = (int)(((u + (L >> 1)) >> logL) & (uint32_t)(B - 1));
+                float g3[3];
+                int bb[3];
 #pragma unroll
-                for (int db = -1; db <= 1; ++db) {
-                    const int b = (b0 + db) & (B - 1);
-                    const int64_t k = (int64_t)((((uint64_t)b * (uint64_t)L - u) + (N >> 1)) & mask) -
-                                      (int64_t)(N >> 1);
-                    const float g = it->Ghat[k < 0 ? -k : k];
-                    atomicAdd((unsigned long long*)&acc[2 * b], (unsigned long long)__float2ll_rn(g * c.x * scale));
-                    atomicAdd((unsigned long long*)&acc[2 * b + 1], (unsigned long long)__float2ll_rn(g * c.y * scale));
+                for (int q = 0; q < 3; ++q) {
+                    bb[q] = (b0 + q - 1) & (B - 1);
+                    const int k = (int)((((uint32_t)bb[q] * L - u) + halfN) & mask) - (int)halfN;
+                    g3[q] = it->Ghat[k < 0 ? -k : k] * scale;
+                }
+                for (int rr = 0; rr < nr; ++rr) {
+                    const uint32_t o_r = (aoff + sigma * (uint32_t)it->tau[r0 + rr]) & mask;
+                    const float2 c = cmul(v, cis_2pi_frac((f * o_r) & mask, n));
+                    long long* ar = wacc + (size_t)rr * per_round;
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        atomicAdd((unsigned long long*)&ar[2 * bb[q]], (unsigned long long)__float2ll_rn(g3[q] * c.x));
+                        atomicAdd((unsigned long long*)&ar[2 * bb[q] + 1], (unsigned long long)__float2ll_rn(g3[q] * c.y));
+                    }
                 }
             }
             __syncthreads();
-            for (int b = tid; b < B; b += T) {
-                float2 yv = Y[(int64_t)r * B + b];
-                yv.x -= __ll2float_rn(acc[2 * b]) * iscale;
-                yv.y -= __ll2float_rn(acc[2 * b + 1]) * iscale;
-                Y[(int64_t)r * B + b] = yv;
+            for (int e = tid; e < nr * B; e += T) {
+                const int rr = e / B, b = e - rr * B;
+                long long sr = 0, si = 0;
+                for (int w = 0; w < nco; ++w) {
+                    const long long* aw = acc + ((size_t)w * rc + rr) * per_round;
+                    sr += aw[2 * b];
+                    si += aw[2 * b + 1];
+                }
+                float2* yp = &Y[(int64_t)(r0 + rr) * B + b];
+                float2 yv = *yp;
+                yv.x -= __ll2float_rn(sr) * iscale;
+                yv.y -= __ll2float_rn(si) * iscale;
+                *yp = yv;
             }
             __syncthreads();
         }
@@ -483,8 +637,8 @@ __global__ void __launch_bounds__(kDecodeThreads) k_decode(const DecodeArgs a) {
     // ---- 2. large-bucket selection (Section 3: buckets with p >= 1) -------------------
     float mx = 0.f;
     for (int b = tid; b < B; b += T) {
-        float2 y0 = Y[b];
-        float k2 = fmaf(y0.x, y0.x, y0.y * y0.y);
+        const float2 y0 = Y[b];
+        const float k2 = fmaf(y0.x, y0.x, y0.y * y0.y);
         key[b] = k2;
         mx = fmaxf(mx, k2);
     }
@@ -507,24 +661,16 @@ __global__ void __launch_bounds__(kDecodeThreads) k_decode(const DecodeArgs a) {
     __syncthreads();
     const float theta = s_theta;
     const int n_c = it->n_c;
-    // threshold T = bits of the n_c-th largest key (keys >= 0 compare as unsigned)
-    uint32_t Tb = 0;
-    if (n_c < B) {
-        for (int bit = 30; bit >= 0; --bit) {
-            const uint32_t trial = Tb | (1u << bit);
-            int c = 0;
-            for (int b = tid; b < B; b += T) c += (__float_as_uint(key[b]) >= trial);
-            int tot = block_count(c, &s_cnt);
-            if (tot >= n_c) Tb = trial;
-        }
-    }
     // each thread owns a contiguous chunk of buckets for order-preserving scans
     const int E = (B + T - 1) / T;
     const int b_lo = min(B, tid * E), b_hi = min(B, b_lo + E);
+    uint32_t Tb = 0;
     int need_ties = 0;
     if (n_c < B) {
+        // T = the n_c-th largest key (keys >= 0 compare as unsigned integers)
+        Tb = block_radix_select(key, b_lo, b_hi, n_c, s_hist, s_bc);
         int gt = 0;
-        for (int b = tid; b < B; b += T) gt += (__float_as_uint(key[b]) > Tb);
+        for (int b = b_lo; b < b_hi; ++b) gt += (__float_as_uint(key[b]) > Tb);
         need_ties = n_c - block_count(gt, &s_cnt);
     }
     // selection flags of this thread's chunk (E <= 4 buckets), ties to the lower b
@@ -552,91 +698,98 @@ __global__ void __launch_bounds__(kDecodeThreads) k_decode(const DecodeArgs a) {
     __syncthreads();
 
     // ---- 3. multiscale location, votes, estimation: one thread per candidate ----------
-    const int l = a.l, qn = a.qn;
+    const int l = a.l;
     const int need = a.min_votes > 0 ? min(a.min_votes, S) : S;
     for (int ci = tid; ci < ncand; ci += T) {
         const int b = cand[ci];
         const float2 y0 = Y[b];
         const float m0 = fmaf(y0.x, y0.x, y0.y * y0.y);
-        uint32_t Phi[kMaxRounds];
-        for (int s = 1; s <= S; ++s) {
-            const float2 ys = Y[(int64_t)s * B + b];
-            const float cr = ys.x * y0.x + ys.y * y0.y;
-            const float cim = ys.y * y0.x - ys.x * y0.y;
-            const float turns = atan2f(cim, cr) * 0.15915494309189535f;
-            Phi[s - 1] = (uint32_t)__float2ll_rn(turns * 4294967296.0f);
-        }
-        int64_t umin = (int64_t)b * L - L;
-        for (int s = 1; s < S; ++s) {
-            const uint64_t ts = (uint64_t)it->tau[s];
-            const uint64_t W = it->W[s - 1];
-            const uint32_t Ap = (uint32_t)((((uint64_t)umin & mask) * ts & mask) << shift);
-            const uint32_t ph = Phi[s - 1];
-            const uint32_t delta = ph - Ap;
-            const int64_t j0 = (int64_t)(((uint64_t)delta * (uint64_t)l) / W);
-            uint32_t bd = 0xffffffffu;
-            int bj = l;
-            const int64_t cands[5] = {j0 - 1, j0, j0 + 1, 0, l - 1};
+        // phases phi_s (2^-32 turns) and magnitude votes of all levels, loaded up front
+        uint32_t ph[RMAX];
+        uint64_t magok = 0;
 #pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                const int64_t j = cands[q];
-                if (j < 0 || j >= l) continue;
-                const uint32_t Ej = Ap + (uint32_t)(((uint64_t)(2 * j + 1) * W + (uint64_t)l) / (uint64_t)(2 * l));
-                const uint32_t d = circ_dist(ph, Ej);
-                if (d < bd || (d == bd && j < bj)) { bd = d; bj = (int)j; }
+        for (int s = 1; s < RMAX; ++s) {
+            if (s <= S) {
+                const float2 ys = Y[(int64_t)s * B + b];
+                ph[s - 1] = phase_fixed(ys, y0);
+                const float ms = fmaf(ys.x, ys.x, ys.y * ys.y);
+                magok |= (fabsf(ms - m0) <= a.mag_tol * m0) ? (1ull << (s - 1)) : 0ull;
             }
-            const int64_t Lb = it->Lbar[s - 1];
-            umin += floor_div(((int64_t)2 * bj * kQDen - qn) * Lb, (int64_t)2 * l * kQDen);
+        }
+        // block levels: region [u_min, u_min + Lbar_s) of l blocks
+        int32_t umin = b * (int32_t)L - (int32_t)L;
+#pragma unroll
+        for (int s = 1; s < RMAX; ++s) {
+            if (s < S) {
+                const uint32_t ts = (uint32_t)it->tau[s];
+                const uint32_t Ap = ((uint32_t)umin * ts) << shift;
+                const int j0 = (int)floorf((float)(ph[s - 1] - Ap) * it->jscale[s - 1]);
+                uint32_t bd = 0xffffffffu;
+                int bj = l;
+#pragma unroll
+                for (int q = 0; q < 7; ++q) {
+                    const int j = q < 5 ? j0 - 2 + q : (q == 5 ? 0 : l - 1);
+                    if (j < 0 || j >= l) continue;
+                    const uint32_t d = circ_dist(ph[s - 1], Ap + it->Cj[s - 1][j]);
+                    if (d < bd || (d == bd && j < bj)) { bd = d; bj = j; }
+                }
+                umin += it->Dj[s - 1][bj];
+            }
         }
         // final level: the Lbar_S integers u_min + i
-        uint64_t ustar;
-        {
-            const uint64_t ts = (uint64_t)it->tau[S];
-            const int64_t Lb = it->Lbar[S - 1];
-            const uint32_t Dl = (uint32_t)it->W[S - 1];
-            const uint32_t P0 = (uint32_t)((((uint64_t)umin & mask) * ts & mask) << shift);
-            const uint32_t ph = Phi[S - 1];
-            const int64_t i0 = (int64_t)((uint32_t)(ph - P0) / Dl);
-            uint32_t bd = 0xffffffffu;
-            int64_t bi = Lb;
-            const int64_t cands[5] = {i0 - 1, i0, i0 + 1, 0, Lb - 1};
+        uint32_t phS = 0;
 #pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                const int64_t i = cands[q];
+        for (int s = 1; s < RMAX; ++s)
+            if (s == S) phS = ph[s - 1];
+        uint32_t ustar;
+        {
+            const uint32_t ts = (uint32_t)it->tau[S];
+            const int Lb = (int)it->Lbar[S - 1];
+            const uint32_t Dl = (uint32_t)it->W[S - 1];
+            const uint32_t P0 = ((uint32_t)umin * ts) << shift;
+            const int i0 = (int)floorf((float)(phS - P0) * it->jscale[S - 1]);
+            uint32_t bd = 0xffffffffu;
+            int bi = Lb;
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                const int i = q < 5 ? i0 - 2 + q : (q == 5 ? 0 : Lb - 1);
                 if (i < 0 || i >= Lb) continue;
-                const uint32_t Pi = P0 + (uint32_t)((uint64_t)i * Dl);
-                const uint32_t d = circ_dist(ph, Pi);
+                const uint32_t d = circ_dist(phS, P0 + (uint32_t)i * Dl);
                 if (d < bd || (d == bd && i < bi)) { bd = d; bi = i; }
             }
-            ustar = (uint64_t)(umin + bi) & mask;
+            ustar = (uint32_t)(umin + bi) & mask;
         }
-        int votes = 0;
-        for (int s = 1; s <= S; ++s) {
-            const uint32_t Ps = (uint32_t)(((ustar * (uint64_t)it->tau[s]) & mask) << shift);
-            const uint32_t d = circ_dist(Phi[s - 1], Ps);
-            const float2 ys = Y[(int64_t)s * B + b];
-            const float ms = fmaf(ys.x, ys.x, ys.y * ys.y);
-            votes += (d <= it->H[s - 1]) && (fabsf(ms - m0) <= a.mag_tol * m0);
+        // votes: phase consistency with u* and magnitude consistency with round 0
+        int nv = 0;
+#pragma unroll
+        for (int s = 1; s < RMAX; ++s) {
+            if (s <= S) {
+                const uint32_t Ps = (ustar * (uint32_t)it->tau[s]) << shift;
+                nv += (circ_dist(ph[s - 1], Ps) <= it->H[s - 1]) && ((magok >> (s - 1)) & 1ull);
+            }
         }
-        const int own = (int)(((ustar + (uint64_t)(L >> 1)) >> logL) & (uint64_t)(B - 1)) == b;
-        const bool accept = votes >= need && own;
-        cvt[ci] = accept ? (int8_t)votes : (int8_t)-1;
+        const bool own = (int)(((ustar + (L >> 1)) >> logL) & (uint32_t)(B - 1)) == b;
+        const bool accept = nv >= need && own;
+        cvt[ci] = accept ? (int8_t)nv : (int8_t)-1;
         if (accept) {
-            const uint64_t f = (sinv * ustar) & mask;
-            const int64_t kb = (int64_t)((((uint64_t)b * (uint64_t)L - ustar) + (N >> 1)) & mask) - (int64_t)(N >> 1);
-            const float g = it->Ghat[kb < 0 ? -kb : kb];
-            const float ig = 1.f / g;
-            float vre[kMaxRounds], vim[kMaxRounds];
-            for (int r = 0; r < R; ++r) {
-                const uint64_t o_r = (aoff + sigma * (uint64_t)it->tau[r]) & mask;
-                const float2 e = cis_2pi_frac((f * o_r) & mask, n);
-                const float2 yr = Y[(int64_t)r * B + b];
-                const float2 v = cmul(yr, make_float2(e.x, -e.y));
-                vre[r] = v.x * ig;
-                vim[r] = v.y * ig;
+            const uint32_t f = (sinv * ustar) & mask;
+            const int kb = (int)((((uint32_t)b * L - ustar) + halfN) & mask) - (int)halfN;
+            const float ig = 1.f / it->Ghat[kb < 0 ? -kb : kb];
+            float vre[RMAX], vim[RMAX];
+#pragma unroll
+            for (int r = 0; r < RMAX; ++r) {
+                if (r < R) {
+                    const uint32_t o_r = (aoff + sigma * (uint32_t)it->tau[r]) & mask;
+                    const float2 e = cis_2pi_frac((f * o_r) & mask, n);
+                    const float2 v = cmul(Y[(int64_t)r * B + b], make_float2(e.x, -e.y));
+                    vre[r] = v.x * ig;
+                    vim[r] = v.y * ig;
+                }
             }
             cf[ci] = (int32_t)f;
-            cv[ci] = make_float2(med_sorted(vre, R), med_sorted(vim, R));
+            const float mre = median_of<RMAX>(vre, R);
+            const float mim = median_of<RMAX>(vim, R);
+            cv[ci] = make_float2(mre, mim);
         }
     }
     __syncthreads();
@@ -668,7 +821,6 @@ __global__ void __launch_bounds__(kDecodeThreads) k_decode(const DecodeArgs a) {
     }
     if (tid == 0) a.F[sig] = F0 + nnew;
 }
-
 
 // ----------------------------------------------------------------- finalize ---------
 // Top-K of the found set by |v| (ties to the lower frequency), sorted by frequency.
@@ -767,8 +919,12 @@ __global__ void __launch_bounds__(1024) k_finalize(const int32_t* Fc, const int3
 }
 
 // ----------------------------------------------------------------- launchers --------
+int configure_kernels();
+
 int launch_bucketize(sfft4_plan_s* p, int mi, int nsig, const float2* x, int64_t x_stride,
                      int32_t signal0, float2* y_out, int64_t y_sig_stride, cudaStream_t st) {
+    int rc0 = configure_kernels();
+    if (rc0) return rc0;
     const IterHost& ih = p->iters[mi];
     const IterDev& d = ih.d;
     for (const FoldGroup& g : ih.groups) {
@@ -782,18 +938,39 @@ int launch_bucketize(sfft4_plan_s* p, int mi, int nsig, const float2* x, int64_t
         a.m = d.m;
         a.signal0 = signal0;
         a.B = d.B;
+        a.logB = d.logB;
         a.Wj = ih.Wj;
         a.h = d.h;
+        a.w = 2 * d.h + 1;
         a.G = d.G;
         a.g = g;
-        for (int s = 0; s < kFoldRG; ++s) a.tau[s] = (s < g.nr) ? d.tau[g.r0 + s] : 0;
+        // rows m' of B with tau_s - h <= rho + m' B <= tau_s + h for some rho in [0, B)
+        int Mrows = 0;
+        for (int s = 0; s < kFoldRG; ++s) {
+            a.tau[s] = (s < g.nr) ? (int32_t)d.tau[g.r0 + s] : 0;
+            int64_t lo = floor_div(a.tau[s] - (int64_t)d.h - (d.B - 1), d.B);
+            int64_t hi = floor_div(a.tau[s] + (int64_t)d.h, d.B);
+            a.mlo[s] = (int32_t)lo;
+            if (s < g.nr) Mrows = std::max<int>(Mrows, (int)(hi - lo + 1));
+        }
+        a.Mrows = Mrows;
+        for (int s = 0; s < kFoldRG; ++s) a.soff[s] = (s * Mrows - a.mlo[s]) * ih.Wj;
         dim3 grid(d.B / ih.Wj, nsig);
         int threads = ih.Wj * g.P;
+        size_t smem = (size_t)g.nr * Mrows * ih.Wj * sizeof(float);
         cudaEvent_t ev = nullptr;
         int rc = prof_begin(p, st, &ev);
         if (rc) return rc;
-        if (g.nr <= 4) k_fold<4><<<grid, threads, 0, st>>>(a);
-        else k_fold<8><<<grid, threads, 0, st>>>(a);
+        switch (g.nr) {
+            case 1: k_fold<1><<<grid, threads, smem, st>>>(a); break;
+            case 2: k_fold<2><<<grid, threads, smem, st>>>(a); break;
+            case 3: k_fold<3><<<grid, threads, smem, st>>>(a); break;
+            case 4: k_fold<4><<<grid, threads, smem, st>>>(a); break;
+            case 5: k_fold<5><<<grid, threads, smem, st>>>(a); break;
+            case 6: k_fold<6><<<grid, threads, smem, st>>>(a); break;
+            case 7: k_fold<7><<<grid, threads, smem, st>>>(a); break;
+            default: k_fold<8><<<grid, threads, smem, st>>>(a); break;
+        }
         rc = prof_end(p, st, ev, kProfFold, g.unique * nsig);
         if (rc) return rc;
     }
@@ -815,6 +992,8 @@ int launch_bucketize(sfft4_plan_s* p, int mi, int nsig, const float2* x, int64_t
 }
 
 int launch_decode(sfft4_plan_s* p, int mi, int nsig, cudaStream_t st) {
+    int rc0 = configure_kernels();
+    if (rc0) return rc0;
     const IterDev& d = p->iters[mi].d;
     DecodeArgs a;
     a.N = (uint64_t)p->N;
@@ -840,11 +1019,13 @@ int launch_decode(sfft4_plan_s* p, int mi, int nsig, cudaStream_t st) {
     a.Hlog = p->Hlog;
     a.theta = p->theta;
     a.fxexp = p->fxexp;
-    size_t smem = 26 * (size_t)d.B;
+    size_t smem = decode_smem(d.B);
     cudaEvent_t ev = nullptr;
     int rc = prof_begin(p, st, &ev);
     if (rc) return rc;
-    k_decode<<<nsig, kDecodeThreads, smem, st>>>(a);
+    if (d.R <= 8) k_decode<8><<<nsig, kDecodeThreads, smem, st>>>(a);
+    else if (d.R <= 16) k_decode<16><<<nsig, kDecodeThreads, smem, st>>>(a);
+    else k_decode<64><<<nsig, kDecodeThreads, smem, st>>>(a);
     rc = check_cuda(cudaGetLastError());
     if (rc) return rc;
     return prof_end(p, st, ev, kProfDecode, 0);
@@ -901,13 +1082,27 @@ int prof_end(sfft4_plan_s* p, cudaStream_t st, cudaEvent_t a, int kind, int64_t 
 }
 
 int configure_kernels() {
-    static bool done = false;
-    if (done) return SFFT4_OK;
-    int rc = check_cuda(cudaFuncSetAttribute(k_decode, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             26 * kBMax));
+    static bool done[64] = {false};
+    int dev = 0;
+    int rc0 = check_cuda(cudaGetDevice(&dev));
+    if (rc0) return rc0;
+    if (dev < 0 || dev >= 64) return SFFT4_ECUDA;
+    if (done[dev]) return SFFT4_OK;
+    int rc = SFFT4_OK;
+    const void* folds[] = {(const void*)k_fold<1>, (const void*)k_fold<2>, (const void*)k_fold<3>,
+                           (const void*)k_fold<4>, (const void*)k_fold<5>, (const void*)k_fold<6>,
+                           (const void*)k_fold<7>, (const void*)k_fold<8>};
+    for (const void* f : folds)
+        if (!rc) rc = check_cuda(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kFoldSmemMax));
+    if (!rc) rc = check_cuda(cudaFuncSetAttribute(k_decode<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)decode_smem(kBMax)));
+    if (!rc) rc = check_cuda(cudaFuncSetAttribute(k_decode<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)decode_smem(kBMax)));
+    if (!rc) rc = check_cuda(cudaFuncSetAttribute(k_decode<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)decode_smem(kBMax)));
     if (!rc) rc = check_cuda(cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   8 * kKMax));
-    if (!rc) done = true;
+    if (!rc) done[dev] = true;
     return rc;
 }
 

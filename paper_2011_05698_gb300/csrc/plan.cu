@@ -196,6 +196,12 @@ int sfft4_plan(sfft4_plan_t* out, int64_t N, int64_t K, int32_t l, double q, uin
     p->o = o;
     p->o.B1 = (int32_t)B1;
     CK(cudaGetDevice(&p->device));
+    if (o.l2_fetch_bytes >= 0) {
+        // The gather reads one 8-byte sample per random 32-byte sector; a larger L2 fetch
+        // granularity would move 2-4x the needed DRAM bytes.  This is a limit of the
+        // calling process's CUDA context (a performance hint), not a device setting.
+        CK(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, o.l2_fetch_bytes ? o.l2_fetch_bytes : 32));
+    }
 
     auto sch = schedule(K, B1, o.max_iters);
     p->Fcap = 0;
@@ -229,20 +235,36 @@ int sfft4_plan(sfft4_plan_t* out, int64_t N, int64_t K, int32_t l, double q, uin
                 d.H[s] = (uint32_t)((((int64_t)(kQDen + qn) * Lb * ts) << (32 - p->n)) /
                                     (2 * (int64_t)l * kQDen));
                 d.W[s] = (uint64_t)(Lb * ts) << (32 - p->n);
+                d.jscale[s] = (float)((double)l / (double)d.W[s]);
+                for (int j = 0; j < l; ++j) {
+                    d.Cj[s][j] = (uint32_t)(((uint64_t)(2 * j + 1) * d.W[s] + (uint64_t)l) / (uint64_t)(2 * l));
+                    int64_t num = ((int64_t)2 * j * kQDen - qn) * Lb, den = (int64_t)2 * l * kQDen;
+                    int64_t fq = num / den;
+                    if (num % den != 0 && num < 0) --fq;
+                    d.Dj[s][j] = (int32_t)fq;
+                }
             } else {
                 ts = N / Lb;
                 d.H[s] = (uint32_t)((ts << (32 - p->n)) / 2);
                 d.W[s] = (uint64_t)ts << (32 - p->n);
+                d.jscale[s] = (float)(1.0 / (double)d.W[s]);
             }
             d.tau[s + 1] = ts;
         }
         // fold groups of up to kFoldRG rounds
-        ih.Wj = (int32_t)std::min<int64_t>(B, 256);
+        // residues per fold CTA: 64, fewer when the staged window rows of a CTA
+        // (rounds x rows x residues floats) would exceed the shared-memory budget
+        ih.Wj = (int32_t)std::min<int64_t>(B, 64);
+        {
+            int64_t rows = (2 * (int64_t)d.h + B) / B + 2;
+            while (ih.Wj > 16 && (int64_t)kFoldRG * rows * ih.Wj * 4 > kFoldSmemMax) ih.Wj >>= 1;
+            if ((int64_t)kFoldRG * rows * ih.Wj * 4 > kFoldSmemMax) { free_plan(p); return SFFT4_EINVAL; }
+        }
         ih.unique = 0;
         for (int r0 = 0; r0 < d.R; r0 += kFoldRG) {
             FoldGroup g;
             build_group(&g, d.tau, r0, std::min(kFoldRG, d.R - r0), d.h);
-            int64_t per = g.unique / (B * 32);
+            int64_t per = (g.unique + B * 12 - 1) / (B * 12);
             g.P = (int32_t)std::max<int64_t>(1, std::min<int64_t>(512 / ih.Wj, per));
             ih.groups.push_back(g);
         }
@@ -341,7 +363,7 @@ int sfft4_get_plan_info(sfft4_plan_t p, sfft4_plan_info* info) {
     info->precision = p->o.precision;
     info->samples_per_transform = p->samples;
     info->found_capacity = p->Fcap;
-    int32_t kpe = 1;
+    int32_t kpe = 1;  // finalize
     for (auto& ih : p->iters) kpe += (int32_t)ih.groups.size() + 2;
     info->kernels_per_execute = kpe;
     return SFFT4_OK;

@@ -20,6 +20,7 @@ constexpr int kBMin = 16;
 constexpr int kBMax = 4096;
 constexpr int kKMax = 4096;
 constexpr int kDecodeThreads = 1024;
+constexpr int kFoldSmemMax = 100 * 1024;     // staged window rows of one fold CTA
 
 // Rounds [r0, r0 + nr) of one iteration that one fold launch accumulates, and the
 // t-segments covering the union of their windows [tau_s - h, tau_s + h]; within a segment
@@ -40,6 +41,9 @@ struct IterDev {
     int64_t tau[kMaxRounds + 1];       // tau_0 = 0 .. tau_S
     uint32_t H[kMaxRounds];            // vote thresholds, levels 1..S at index 0..S-1
     uint64_t W[kMaxRounds];            // phase span (Lbar_s tau_s) << (32 - n) of level s
+    float jscale[kMaxRounds];          // l / W (block levels), 1 / W (final level)
+    uint32_t Cj[kMaxRounds][32];       // block centre offsets ((2j+1) W + l) / (2l)
+    int32_t Dj[kMaxRounds][32];        // region shifts floor((2jQ - q_n) Lbar_s / (2lQ))
     const float* G;                    // w = 2h + 1 window coefficients G_{-h..h}
     const float* Ghat;                 // G'^_k for k = 0..3L/2
     const float2* tw;                  // e^{-2 pi i k / B}, k < B/2
