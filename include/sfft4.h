@@ -203,6 +203,31 @@ typedef struct {
 
 SFFT4_API int sfft4_profile_get(sfft4_plan_t plan, sfft4_profile* out, int32_t reset);
 
+/*
+ * sfft4_window_noalloc -- the flat window tables of sfft4_plan (G: 2h+1 float32
+ * coefficients G_{-h..h}; Ghat: 3L/2+1 float32 values G'^_k, k = 0..3L/2, L = N/B) computed
+ * into caller-provided device buffers without allocating any device memory.  The paper has
+ * no counterpart: this entry point serves callers that cannot allocate device memory at the
+ * point where they need the tables, because their memory is owned by another allocator (a
+ * framework's caching allocator or a fixed pool) or because they cannot afford the implicit
+ * device synchronisation of cudaMalloc/cudaFree.
+ *   N, B, delta  as for sfft4_plan (N a power of two in [2^8, 2^30]; B a power of two in
+ *                [16, min(4096, N/64)]; 0 < delta < 1/2)
+ *   G_dev, Ghat_dev  device outputs with capacities G_cap >= 2h+1 and Ghat_cap >= 3L/2+1
+ *                elements (h = ceil(B 4 sqrt2 erfcinv(delta) / (2 pi) * sqrt(2 ln(1/delta))))
+ *   stream       cudaStream_t or NULL; the work is asynchronous on it
+ * Its only scratch is one static device array of 131072 FP64 values (1 MiB, held by every GPU
+ * that loads the library until the process exits), so windows longer than 131072
+ * coefficients (B > 2048 at delta = 1e-8) are rejected with SFFT4_EINVAL.  The first call on
+ * a device looks up that array's address (cudaGetSymbolAddress) once; make that first call
+ * before any stream capture.  All calls share the array: calls that overlap on the GPU (on
+ * different streams, or from different host threads) race and must be serialised by the
+ * caller.
+ * Errors: SFFT4_EINVAL (sizes, capacities, NULL outputs), SFFT4_ECUDA.
+ */
+SFFT4_API int sfft4_window_noalloc(int64_t N, int32_t B, double delta, float* G_dev, int64_t G_cap,
+                                   float* Ghat_dev, int64_t Ghat_cap, void* stream);
+
 /* Text of an error code (static storage). */
 SFFT4_API const char* sfft4_strerror(int code);
 
