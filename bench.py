@@ -287,11 +287,18 @@ def main():
     traffic = None
     if tr is not None:
         traffic = tr["dram_bytes_per_sample"] * prof["fold_samples"] / launches
+    # achievable rate of the gather's access pattern (random 8-byte loads inside each signal
+    # of this same batch), measured on this device
+    gather_lps = s4.gather_probe(xs)
+    gather_ceiling = 32.0 * gather_lps / 1e9  # GB/s of 32-byte sectors
+    sector_gbs = 4.0 * achieved
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "k_fold (permuted gather + window + fold)",
                 "per_unit": "8 B per distinct sample read (complex64)",
                 "sector_frac": 4.0 * achieved / peak, "peak_kind": peak_kind,
+                "random_gather_ceiling_gbs": gather_ceiling,
+                "frac_of_random_gather_ceiling": sector_gbs / gather_ceiling if gather_ceiling > 0 else None,
                 "fold_share_of_step": prof["fold_ms"] / (1e3 * el) if el > 0 else None,
                 "kernel_ms": {k: prof[k + "_ms"] for k in ("fold", "fft", "decode", "finalize")}}
 

@@ -204,6 +204,20 @@ typedef struct {
 SFFT4_API int sfft4_profile_get(sfft4_plan_t plan, sfft4_profile* out, int32_t reset);
 
 /*
+ * sfft4_gather_probe -- measures the device's throughput for the memory access pattern of
+ * the gather (Lemma 1, step P0): independent random 8-byte loads, each CTA confined to one
+ * signal of a batch.  Used as the achievable-bandwidth denominator of the gather's
+ * roofline.  Reads x_dev (nsig signals of N complex64 at stride x_stride, N a power of two
+ * <= 2^30); sink_dev is one float the kernel may write.  `blocks` CTAs of 512 threads each
+ * issue iters x 4 loads; the timed launch follows one warm-up launch on `stream`.
+ * Writes loads per second to *loads_per_second (host).  Synchronises with the stream.
+ * Errors: SFFT4_EINVAL, SFFT4_ECUDA.
+ */
+SFFT4_API int sfft4_gather_probe(const void* x_dev, int32_t nsig, int64_t N, int64_t x_stride,
+                                 float* sink_dev, int32_t blocks, int32_t iters,
+                                 double* loads_per_second, void* stream);
+
+/*
  * sfft4_window_noalloc -- the flat window tables of sfft4_plan (G: 2h+1 float32
  * coefficients G_{-h..h}; Ghat: 3L/2+1 float32 values G'^_k, k = 0..3L/2, L = N/B) computed
  * into caller-provided device buffers without allocating any device memory.  The paper has

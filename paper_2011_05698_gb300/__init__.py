@@ -15,11 +15,26 @@ import ctypes
 from . import _lib
 from ._lib import Sfft4Error, check  # noqa: F401
 
-__all__ = ["Plan", "Sfft4Error", "load"]
+__all__ = ["Plan", "Sfft4Error", "load", "gather_probe"]
 
 
 def load():
     return _lib.load()
+
+
+def gather_probe(xs, blocks=None, iters=64):
+    """Random 8-byte gathers per second within each row of xs (CUDA complex64, (nsig, N)):
+    the achievable rate of the gather's access pattern on this device."""
+    import torch
+    lib = _lib.load()
+    if blocks is None:
+        blocks = torch.cuda.get_device_properties(xs.device).multi_processor_count * 8
+    sink = torch.zeros(1, dtype=torch.float32, device=xs.device)
+    out = ctypes.c_double()
+    check(lib.sfft4_gather_probe(ctypes.c_void_p(xs.data_ptr()), xs.shape[0], xs.shape[1], xs.stride(0),
+                                 ctypes.c_void_p(sink.data_ptr()), blocks, iters, ctypes.byref(out),
+                                 _stream_ptr(xs.device)), "sfft4_gather_probe")
+    return out.value
 
 
 def _stream_ptr(device):

@@ -67,6 +67,8 @@ SIGNATURES = [
     ("sfft4_bucketize", ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P]),
     ("sfft4_trace_get", ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, _P, _P, _P, _P]),
     ("sfft4_profile_get", ctypes.c_int, [_P, ctypes.POINTER(Profile), ctypes.c_int32]),
+    ("sfft4_gather_probe", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _P,
+                                          ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), _P]),
     ("sfft4_window_noalloc", ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_double, _P,
                                             ctypes.c_int64, _P, ctypes.c_int64, _P]),
     ("sfft4_strerror", ctypes.c_char_p, [ctypes.c_int]),
