@@ -38,6 +38,7 @@ extern "C" {
 #define SFFT4_ENOMEM (-2)   /* device or host allocation failed                        */
 #define SFFT4_ECUDA (-3)    /* a CUDA runtime call failed (details: sfft4_last_cuda_error) */
 #define SFFT4_ESTATE (-4)   /* call not valid in the plan's current state               */
+#define SFFT4_ETIMEOUT (-5) /* a bounded device-side wait gave up (see sfft4_sync_status) */
 
 /* ----------------------------------------------------------------- precision ------ */
 #define SFFT4_FP32 0        /* window, fold and B-point DFT in FP32 (CUDA cores)         */
@@ -241,6 +242,14 @@ SFFT4_API int sfft4_gather_probe(const void* x_dev, int32_t nsig, int64_t N, int
  */
 SFFT4_API int sfft4_window_noalloc(int64_t N, int32_t B, double delta, float* G_dev, int64_t G_cap,
                                    float* Ghat_dev, int64_t Ghat_cap, void* stream);
+
+/*
+ * sfft4_sync_status -- synchronises the device and reports whether any bounded device-side
+ * wait of this plan's kernels (the tensor-core DFT's wait for its accumulator) gave up since
+ * the last call: SFFT4_ETIMEOUT if so (the affected outputs are incomplete), else SFFT4_OK.
+ * Clears the flag.  Errors: SFFT4_EINVAL (NULL plan), SFFT4_ECUDA.
+ */
+SFFT4_API int sfft4_sync_status(sfft4_plan_t plan);
 
 /* Text of an error code (static storage). */
 SFFT4_API const char* sfft4_strerror(int code);

@@ -114,6 +114,10 @@ class Plan:
                                            Gh.ctypes.data_as(ctypes.c_void_p)), "sfft4_get_window")
         return G, Gh
 
+    def sync_status(self):
+        """Synchronise and raise if a bounded device wait of this plan gave up."""
+        check(_lib.load().sfft4_sync_status(self._h), "sfft4_sync_status")
+
     def profile(self, reset=True):
         """Per-kernel launch counts and CUDA-event times since the last reset (profile=True)."""
         pr = _lib.Profile()

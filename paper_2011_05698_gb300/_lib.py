@@ -11,6 +11,7 @@ SFFT4_EINVAL = -1
 SFFT4_ENOMEM = -2
 SFFT4_ECUDA = -3
 SFFT4_ESTATE = -4
+SFFT4_ETIMEOUT = -5
 SFFT4_FP32 = 0
 SFFT4_BF16X3 = 1
 MAX_ROUNDS = 64
@@ -71,6 +72,7 @@ SIGNATURES = [
                                           ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), _P]),
     ("sfft4_window_noalloc", ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_double, _P,
                                             ctypes.c_int64, _P, ctypes.c_int64, _P]),
+    ("sfft4_sync_status", ctypes.c_int, [_P]),
     ("sfft4_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("sfft4_last_cuda_error", ctypes.c_char_p, []),
 ]

@@ -984,9 +984,15 @@ int launch_bucketize(sfft4_plan_s* p, int mi, int nsig, const float2* x, int64_t
     cudaEvent_t ev = nullptr;
     int rc = prof_begin(p, st, &ev);
     if (rc) return rc;
-    k_fft<<<blocks, T, smem, st>>>(p->z, y_out, B, logB, d.tw, (int64_t)p->R_max * p->B_max,
-                                   y_sig_stride, R, cpc, ncols);
-    rc = check_cuda(cudaGetLastError());
+    if (p->o.precision == SFFT4_BF16X3) {
+        const Window& w = p->wins[ih.win];
+        rc = launch_dft_tc(p->z, (int64_t)p->R_max * p->B_max, p->u, y_out, y_sig_stride, nsig, R, B,
+                           w.dA1, w.dA2, w.tw4, p->status, p->sm_count, st);
+    } else {
+        k_fft<<<blocks, T, smem, st>>>(p->z, y_out, B, logB, d.tw, (int64_t)p->R_max * p->B_max,
+                                       y_sig_stride, R, cpc, ncols);
+        rc = check_cuda(cudaGetLastError());
+    }
     if (rc) return rc;
     return prof_end(p, st, ev, kProfFft, 0);
 }
@@ -1102,6 +1108,7 @@ int configure_kernels() {
                                                   (int)decode_smem(kBMax)));
     if (!rc) rc = check_cuda(cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   8 * kKMax));
+    if (!rc) rc = configure_dft_tc();
     if (!rc) done[dev] = true;
     return rc;
 }
@@ -1171,6 +1178,21 @@ int sfft4_bucketize(sfft4_plan_t p, const void* x_dev, int32_t signal, int32_t m
     const IterDev& d = p->iters[m - 1].d;
     return launch_bucketize(p, m - 1, 1, (const float2*)x_dev, p->N, signal, (float2*)y_dev,
                             (int64_t)d.R * d.B, (cudaStream_t)stream);
+}
+
+int sfft4_sync_status(sfft4_plan_t p) {
+    if (!p) return SFFT4_EINVAL;
+    int rc = check_cuda(cudaDeviceSynchronize());
+    if (rc) return rc;
+    int32_t st = 0;
+    rc = check_cuda(cudaMemcpy(&st, p->status, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (rc) return rc;
+    if (st) {
+        rc = check_cuda(cudaMemset(p->status, 0, sizeof(int32_t)));
+        if (rc) return rc;
+        return SFFT4_ETIMEOUT;
+    }
+    return SFFT4_OK;
 }
 
 int sfft4_profile_get(sfft4_plan_t p, sfft4_profile* out, int32_t reset) {

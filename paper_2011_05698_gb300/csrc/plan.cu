@@ -118,8 +118,11 @@ void free_plan(sfft4_plan_s* p) {
         cudaFree(w.G);
         cudaFree(w.Ghat);
         cudaFree(w.tw);
+        cudaFree(w.dA1);
+        cudaFree(w.dA2);
+        cudaFree(w.tw4);
     }
-    void* bufs[] = {p->iters_dev, p->z, p->y, p->F, p->ff, p->fv, p->fvotes, p->hkeys,
+    void* bufs[] = {p->iters_dev, p->z, p->y, p->u, p->status, p->F, p->ff, p->fv, p->fvotes, p->hkeys,
                     p->hvals, p->theta, p->fxexp, p->trace_y, p->trace_F, p->trace_ff,
                     p->trace_fv, p->trace_votes};
     for (void* b : bufs) cudaFree(b);
@@ -304,9 +307,17 @@ int sfft4_plan(sfft4_plan_t* out, int64_t N, int64_t K, int32_t l, double q, uin
     }
     p->Hlog = ilog2(2 * p->Fcap + 2);
 
+    CK(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device));
     for (auto& w : p->wins) {
         int rc = build_window_tables(p, &w, o.delta);
         if (rc != SFFT4_OK) { free_plan(p); return rc; }
+        if (o.precision == SFFT4_BF16X3) {
+            CK(cudaMalloc(&w.dA1, dft_tc_matrix_bytes()));
+            CK(cudaMalloc(&w.dA2, dft_tc_matrix_bytes()));
+            CK(cudaMalloc(&w.tw4, (size_t)w.B * sizeof(float2)));
+            rc = build_dft_tc_tables(w.B, w.dA1, w.dA2, w.tw4);
+            if (rc != SFFT4_OK) { free_plan(p); return rc; }
+        }
     }
     for (auto& ih : p->iters) {
         const Window& w = p->wins[ih.win];
@@ -325,6 +336,9 @@ int sfft4_plan(sfft4_plan_t* out, int64_t N, int64_t K, int32_t l, double q, uin
     CK(cudaMalloc(&p->z, mb * rb * sizeof(float2)));
     CK(cudaMalloc(&p->y, mb * rb * sizeof(float2)));
     CK(cudaMalloc(&p->F, mb * sizeof(int32_t)));
+    CK(cudaMalloc(&p->status, sizeof(int32_t)));
+    CK(cudaMemset(p->status, 0, sizeof(int32_t)));
+    if (o.precision == SFFT4_BF16X3) CK(cudaMalloc(&p->u, mb * rb * sizeof(float2)));
     CK(cudaMalloc(&p->ff, mb * p->Fcap * sizeof(int32_t)));
     CK(cudaMalloc(&p->fv, mb * p->Fcap * sizeof(double2)));
     CK(cudaMalloc(&p->fvotes, mb * p->Fcap * sizeof(int8_t)));
@@ -413,6 +427,7 @@ const char* sfft4_strerror(int code) {
         case SFFT4_ENOMEM: return "out of memory";
         case SFFT4_ECUDA: return "CUDA error";
         case SFFT4_ESTATE: return "invalid plan state";
+        case SFFT4_ETIMEOUT: return "a bounded device wait gave up";
         default: return "unknown error";
     }
 }

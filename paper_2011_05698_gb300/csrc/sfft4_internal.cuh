@@ -55,6 +55,10 @@ struct Window {
     float* G = nullptr;        // device, 2h + 1
     float* Ghat = nullptr;     // device, 3L/2 + 1
     float2* tw = nullptr;      // device, B/2
+    // tensor-core DFT (precision SFFT4_BF16X3): split DFT matrices of both stages, twiddles
+    unsigned char* dA1 = nullptr;
+    unsigned char* dA2 = nullptr;
+    float2* tw4 = nullptr;     // device, B
 };
 
 struct IterHost {
@@ -147,6 +151,9 @@ struct sfft4_plan_s {
     int8_t* fvotes = nullptr;   // [sig][Fcap]
     int32_t* hkeys = nullptr;   // [sig][2^Hlog] hash keys (frequency or -1)
     int32_t* hvals = nullptr;   // [sig][2^Hlog] entry index
+    float2* u = nullptr;        // [sig][R_max][B_max] four-step scratch (BF16X3 DFT)
+    int32_t* status = nullptr;  // 1 when a bounded device wait gave up
+    int sm_count = 0;
     float* theta = nullptr;     // [sig] candidate floor
     int32_t* fxexp = nullptr;   // [sig] fixed-point exponent of the bucket update
     // trace of signal 0 (opts.trace)
@@ -181,4 +188,11 @@ int prof_begin(sfft4_plan_s* p, cudaStream_t st, cudaEvent_t* a);
 int prof_end(sfft4_plan_s* p, cudaStream_t st, cudaEvent_t a, int kind, int64_t samples);
 enum { kProfFold = 0, kProfFft = 1, kProfDecode = 2, kProfFinalize = 3 };
 int check_cuda(cudaError_t e);
+// Implemented in dft_tc.cu.
+size_t dft_tc_matrix_bytes();
+int build_dft_tc_tables(int B, unsigned char* A1, unsigned char* A2, float2* tw4);
+int configure_dft_tc();
+int launch_dft_tc(const float2* z, int64_t z_stride, float2* u, float2* y, int64_t y_stride, int nsig,
+                  int R, int B, const unsigned char* A1, const unsigned char* A2, const float2* tw4,
+                  int32_t* status, int sm_count, cudaStream_t st);
 }  // namespace sfft4

@@ -74,9 +74,9 @@ def test_window_tables_match_oracle(s4, name):
     p.close()
 
 
-def bucket_parity(s4, N, K, l, q, B1, seed, snr, ms, signal=0):
+def bucket_parity(s4, N, K, l, q, B1, seed, snr, ms, signal=0, precision="fp32"):
     sig = sparse_signal(N, K, seed, snr)
-    p = s4.Plan(N, K, l, q, seed=seed, B1=B1)
+    p = s4.Plan(N, K, l, q, seed=seed, B1=B1, precision=precision)
     op = oracle_plan(N, K, l, q, seed, B1)
     wc = OW.WindowCache(N, op.delta)
     xd = to_dev(sig.x)
@@ -94,6 +94,7 @@ def bucket_parity(s4, N, K, l, q, B1, seed, snr, ms, signal=0):
             rms = np.linalg.norm(Yo[s]) / math.sqrt(it.B)
             assert rel < 5e-6, (m, s, rel)
             assert np.max(np.abs(Yg[s] - Yo[s])) < 2e-5 * rms, (m, s)
+    p.sync_status()
     p.close()
     return worst
 
@@ -102,6 +103,36 @@ def bucket_parity(s4, N, K, l, q, B1, seed, snr, ms, signal=0):
 def test_bucketize_parity(s4, name, snr, ms):
     N, K, l, q, B1 = CONFIGS[name]
     bucket_parity(s4, N, K, l, q, B1, seed=11, snr=snr, ms=ms)
+
+
+@pytest.mark.parametrize("name,snr,ms", [("c1", None, [1, 2, 5]), ("c2", 20.0, [1, 4, 8]), ("c3", None, [1, 3, 6])])
+def test_bucketize_parity_bf16x3(s4, name, snr, ms):
+    """The tensor-core BF16x3 split DFT keeps the bucket arrays within the FP32 bound of
+    the FP64 oracle (single-stage B <= 64 and four-step B > 64 both covered)."""
+    N, K, l, q, B1 = CONFIGS[name]
+    bucket_parity(s4, N, K, l, q, B1, seed=11, snr=snr, ms=ms, precision="bf16x3")
+
+
+def test_bf16x3_matches_fp32_dft(s4):
+    """Every bucket count of the schedule: the tensor-core DFT agrees with the FP32 FFT."""
+    N, K, l, q, B1 = CONFIGS["c3"]
+    sig = sparse_signal(N, K, 2, None)
+    xd = to_dev(sig.x)
+    pf = s4.Plan(N, K, l, q, seed=2, B1=B1)
+    pt = s4.Plan(N, K, l, q, seed=2, B1=B1, precision="bf16x3")
+    seen = set()
+    for m in range(1, pf.info["n_iters"] + 1):
+        B = pf.iter_info(m)["B"]
+        if B in seen:
+            continue
+        seen.add(B)
+        yf = pf.bucketize(xd, m).cpu().numpy().astype(np.complex128)
+        yt = pt.bucketize(xd, m).cpu().numpy().astype(np.complex128)
+        rel = np.linalg.norm(yt - yf) / np.linalg.norm(yf)
+        assert rel < 2e-6, (B, rel)
+    pt.sync_status()
+    pf.close()
+    pt.close()
 
 
 def test_bucketize_parity_other_signal_index(s4):
@@ -113,10 +144,10 @@ FRAGILE_TURNS = 1 << 12      # 2^-20 turns: FP32 phases of FP32 buckets resolve 
 FRAGILE_REL = 1e-5           # relative margin of magnitude and selection decisions
 
 
-def e2e(s4, name, seed, snr=None, trace=False):
+def e2e(s4, name, seed, snr=None, trace=False, precision="fp32"):
     N, K, l, q, B1 = CONFIGS[name]
     sig = sparse_signal(N, K, seed, snr)
-    p = s4.Plan(N, K, l, q, seed=seed, B1=B1, trace=trace)
+    p = s4.Plan(N, K, l, q, seed=seed, B1=B1, trace=trace, precision=precision)
     idx, val, nf, votes = p.execute(to_dev(sig.x))
     n = int(nf.item())
     g = (idx[:n].cpu().numpy(), val[:n].cpu().numpy(), votes[:n].cpu().numpy(), idx.cpu().numpy(), val.cpu().numpy())
@@ -157,12 +188,13 @@ def explain_divergence(p, r, name, seed):
     return None
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
 @pytest.mark.parametrize("name,seeds", [("c1", range(4)), ("c2", range(2)), ("c3", range(2))])
-def test_end_to_end_noiseless(s4, name, seeds):
+def test_end_to_end_noiseless(s4, name, seeds, precision):
     """Noiseless: GPU support = oracle support = generator support; values within 1e-5 of
     the oracle; votes equal unless the runs part at a fragile decision (explained)."""
     for seed in seeds:
-        sig, (f, v, vt, idx_all, val_all), r, p = e2e(s4, name, seed, trace=True)
+        sig, (f, v, vt, idx_all, val_all), r, p = e2e(s4, name, seed, trace=True, precision=precision)
         assert np.array_equal(f, r["f"]), seed
         assert np.array_equal(f, sig.freqs), seed
         if not np.array_equal(vt, r["votes"]):
