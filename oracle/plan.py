@@ -173,6 +173,9 @@ def make_plan(N, K, l, q, seed, B1=0, delta=1e-8, select_factor=2.0, min_votes=0
         raise ValueError("need 0 < delta < 1/2")
     if B1 == 0:
         B1 = max(B_MIN, min(4096, N // 64, pow2ceil(2 * K)))
+        # reading R14: halve the default until the window of B1 buckets fits in N/2
+        while B1 > B_MIN and 2 * window_halfwidth(N, B1, delta)[0] + 1 > N // 2:
+            B1 //= 2
     if B1 < B_MIN or B1 & (B1 - 1) or B1 > N // 64 or B1 > 4096:
         raise ValueError("B1 must be a power of two in [16, min(4096, N/64)]")
     its = []

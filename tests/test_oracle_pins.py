@@ -380,3 +380,30 @@ def test_generator_snr_and_support():
     mask = np.ones(clean.N, bool)
     mask[clean.freqs] = False
     assert np.max(np.abs(X[mask])) < 1e-6
+
+
+@pytest.mark.parametrize("N,K,want_B1", [(2**14, 256, 128), (2**16, 600, 512), (2**16, 1024, 512)])
+def test_dense_default_B1_fits_window_and_recovers(N, K, want_B1):
+    """K > N/256: the default B1 is the largest power of two whose window fits in N/2 (the
+    window of N/64 buckets would not), and the longer static schedule still recovers the
+    generator's support exactly."""
+    pl = P.make_plan(N, K, 16, 1.0, seed=1)
+    assert pl.B1 == want_B1
+    assert 2 * P.window_halfwidth(N, 2 * pl.B1, pl.delta)[0] + 1 > N // 2
+    assert all(2 * it.h + 1 <= N // 2 for it in pl.iters)
+    sig = sparse_signal(N, K, 3)
+    r = sfft4.run(sig.x.astype(np.complex128), pl)
+    assert np.array_equal(r["f"], sig.freqs)
+
+
+def test_uneven_sizes_recipe():
+    """The uneven-batch size generator: N powers of two in [2^16, 2^22], K in [10, 2000]
+    capped at N/64, SNR in [10, 40] dB; every drawn size has a valid default plan."""
+    from synth.signals import uneven_sizes
+    Ns, Ks, snrs = uneven_sizes(512, 7)
+    assert np.all((Ns & (Ns - 1)) == 0) and Ns.min() >= 2**16 and Ns.max() <= 2**22
+    assert np.all(Ks >= 10) and np.all(Ks <= 2000) and np.all(Ks <= Ns // 64)
+    assert min(snrs) >= 10.0 and max(snrs) <= 40.0
+    assert len(set(Ns.tolist())) == 7
+    for N, K in sorted(set(zip(Ns.tolist(), Ks.tolist()))):
+        P.make_plan(N, K, 16, 1.0, seed=0)
