@@ -172,24 +172,11 @@ def fold_traffic_record():
 
 def device_batch(N, K, S, seed0, snr, device):
     """Seeded synthetic batch synthesised on the device (spectra drawn by synth)."""
-    import numpy as np
     import torch
-    from synth.signals import spectrum, snr_noise_std
+    from synth.signals import device_signal
     xs = torch.empty((S, N), dtype=torch.complex64, device=device)
     for i in range(S):
-        f, v, _ = spectrum(N, K, seed0 + i)
-        X = torch.zeros(N, dtype=torch.complex128, device=device)
-        X[torch.from_numpy(f).to(device)] = torch.from_numpy(v).to(device)
-        x = torch.fft.ifft(X) * N
-        if snr is not None:
-            g = torch.Generator(device=device)
-            g.manual_seed(seed0 + i)
-            std = float(snr_noise_std(v, snr))
-            nr = torch.randn(N, generator=g, device=device, dtype=torch.float64)
-            ni = torch.randn(N, generator=g, device=device, dtype=torch.float64)
-            x = x + std * torch.complex(nr, ni)
-        xs[i] = x.to(torch.complex64)
-    del np
+        device_signal(N, K, seed0 + i, snr, device, out=xs[i])
     return xs
 
 

@@ -54,7 +54,9 @@ typedef struct {
 /* Plan options; a zero field means "default".  Fill with sfft4_opts_default(). */
 typedef struct {
     int32_t B1;              /* buckets of iteration 1 (power of two, 16..4096, <= N/64);
-                                default pow2ceil(2K) capped at min(4096, N/64)            */
+                                default pow2ceil(2K) capped at min(4096, N/64), then halved
+                                while the window (about 44 B1 samples at delta 1e-8) is wider
+                                than N/2                                                   */
     double delta;            /* flat-window leakage delta of Eq. 9; default 1e-8          */
     int32_t precision;       /* SFFT4_FP32 (default) or SFFT4_BF16X3                      */
     int32_t min_votes;       /* levels that must vote to accept; default = all levels     */
@@ -73,6 +75,12 @@ typedef struct {
                                 process's CUDA context (cudaLimitMaxL2FetchGranularity):
                                 0 = 32 bytes (one sector per gathered sample), negative =
                                 leave the context's limit unchanged                        */
+    int32_t graph;           /* nonzero: the first execute with a given set of buffers and
+                                batch size captures its launch sequence as a CUDA graph;
+                                later executes with the same buffers replay it (one graph
+                                launch).  Ignored when profile or trace is set.  The graph
+                                holds the buffer addresses: the caller keeps them valid
+                                while the plan may replay it                              */
 } sfft4_opts;
 
 /* Fills *opts with the defaults above.  Returns SFFT4_EINVAL if opts is NULL. */
@@ -127,6 +135,49 @@ SFFT4_API int sfft4_execute(sfft4_plan_t plan, const void* x_dev, int64_t* idx_d
 SFFT4_API int sfft4_execute_batched(sfft4_plan_t plan, int32_t nsig, const void* x_dev, int64_t x_stride,
                           int64_t* idx_dev, sfft4_c128* val_dev, int64_t* nfound_dev,
                           int8_t* votes_dev, void* stream);
+
+/*
+ * sfft4_plan_batched -- plan of nsig transforms of different sizes, executed together
+ * (batch of independent problems; each signal follows its own static schedule of Section 3.1).
+ *   N[i], K[i]  size and sparsity of signal i, each within sfft4_plan's limits
+ *   l, q, seed, opts  as for sfft4_plan, shared by every signal (opts.max_batch is ignored)
+ * Signals with equal (N, K) share one schedule; window tables are shared by (N, B).  Level m
+ * of an execute runs iteration m of every signal that has one, as one fold launch per
+ * rounds-per-group count, one DFT launch per bucket count and one decode launch per
+ * round-count class, taking their work from job tables built here.  Signal i uses Philox
+ * counter (i, m, 0, 0), so it matches sfft4_plan(N[i], K[i], ...) run as signal i.
+ * Errors: SFFT4_EINVAL (NULL pointers, nsig < 1, any size invalid), SFFT4_ENOMEM, SFFT4_ECUDA.
+ */
+SFFT4_API int sfft4_plan_batched(sfft4_plan_t* out, int32_t nsig, const int64_t* N, const int64_t* K,
+                                 int32_t l, double q, uint64_t seed, const sfft4_opts* opts);
+
+/*
+ * sfft4_execute_batched_v -- execute a plan from sfft4_plan_batched.
+ *   x_ptrs_dev  device array of nsig device pointers; signal i has N[i] complex64 samples
+ *               (8-byte aligned) at x_ptrs_dev[i].  The array is read by the kernels, so its
+ *               entries may change between executes (also under opts.graph)
+ *   idx_dev     nsig * Kmax int64, val_dev nsig * Kmax complex128, votes_dev nsig * Kmax int8
+ *               (may be NULL), nfound_dev nsig int64; row i (length Kmax = max K[i]) belongs
+ *               to signal i, entries past its K[i] are -1 / 0
+ * Errors: SFFT4_EINVAL (NULL pointers), SFFT4_ESTATE (plan not from sfft4_plan_batched),
+ * SFFT4_ECUDA.
+ */
+SFFT4_API int sfft4_execute_batched_v(sfft4_plan_t plan, const void* const* x_ptrs_dev, int64_t* idx_dev,
+                                      sfft4_c128* val_dev, int64_t* nfound_dev, int8_t* votes_dev,
+                                      void* stream);
+
+typedef struct {
+    int32_t nsig;
+    int32_t n_classes;          /* distinct (N, K) */
+    int32_t n_levels;           /* longest schedule */
+    int32_t kernels_per_execute;
+    int64_t Kmax;               /* output row length */
+    int64_t samples_per_execute;  /* distinct x positions read, summed over signals */
+    int32_t precision;
+} sfft4_batch_info;
+
+/* Summary of a plan from sfft4_plan_batched.  Errors: SFFT4_EINVAL, SFFT4_ESTATE. */
+SFFT4_API int sfft4_get_batch_info(sfft4_plan_t plan, sfft4_batch_info* info);
 
 /* ----------------------------------------------------------------- introspection -- */
 typedef struct {

@@ -8,6 +8,9 @@ every call raises.
     plan = Plan(N=2**22, K=1000, l=16, q=1.0, seed=7, max_batch=64)
     idx, val, nfound, votes = plan.execute(x)            # x: cuda complex64, length N
     idx, val, nfound, votes = plan.execute_batched(xs)   # xs: cuda complex64, (nsig, N)
+
+    bp = BatchPlan(Ns, Ks, l=16, q=1.0, seed=7)          # signals of different N_i, K_i
+    idx, val, nfound, votes = bp.execute(xs)             # xs: list of cuda complex64 tensors
 """
 
 import ctypes
@@ -15,7 +18,7 @@ import ctypes
 from . import _lib
 from ._lib import Sfft4Error, check  # noqa: F401
 
-__all__ = ["Plan", "Sfft4Error", "load", "gather_probe"]
+__all__ = ["Plan", "BatchPlan", "Sfft4Error", "load", "gather_probe"]
 
 
 def load():
@@ -42,30 +45,43 @@ def _stream_ptr(device):
     return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
 
 
+def _opts(B1=0, delta=1e-8, precision="fp32", min_votes=0, select_factor=2.0, sig_floor=1e-10,
+          mag_tol=0.5, max_iters=64, max_batch=1, trace=False, profile=False, graph=False):
+    o = _lib.Opts()
+    check(_lib.load().sfft4_opts_default(ctypes.byref(o)), "sfft4_opts_default")
+    o.B1 = B1
+    o.delta = delta
+    o.precision = {"fp32": _lib.SFFT4_FP32, "bf16x3": _lib.SFFT4_BF16X3}[precision]
+    o.min_votes = min_votes
+    o.select_factor = select_factor
+    o.sig_floor = sig_floor
+    o.mag_tol = mag_tol
+    o.max_iters = max_iters
+    o.max_batch = max_batch
+    o.trace = int(bool(trace))
+    o.profile = int(bool(profile))
+    o.graph = int(bool(graph))
+    return o
+
+
+def _device(device):
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("sFFT4 needs a CUDA device")
+    return torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+
+
 class Plan:
     """A static sFFT4.0 plan (Section 3.1) for one (N, K, l, q, seed)."""
 
     def __init__(self, N, K, l=16, q=1.0, seed=0, *, B1=0, delta=1e-8, precision="fp32",
                  min_votes=0, select_factor=2.0, sig_floor=1e-10, mag_tol=0.5, max_iters=64,
-                 max_batch=1, trace=False, profile=False, device=None):
+                 max_batch=1, trace=False, profile=False, graph=False, device=None):
         import torch
         lib = _lib.load()
-        if not torch.cuda.is_available():
-            raise RuntimeError("sFFT4 needs a CUDA device")
-        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
-        o = _lib.Opts()
-        check(lib.sfft4_opts_default(ctypes.byref(o)), "sfft4_opts_default")
-        o.B1 = B1
-        o.delta = delta
-        o.precision = {"fp32": _lib.SFFT4_FP32, "bf16x3": _lib.SFFT4_BF16X3}[precision]
-        o.min_votes = min_votes
-        o.select_factor = select_factor
-        o.sig_floor = sig_floor
-        o.mag_tol = mag_tol
-        o.max_iters = max_iters
-        o.max_batch = max_batch
-        o.trace = int(bool(trace))
-        o.profile = int(bool(profile))
+        self.device = _device(device)
+        o = _opts(B1, delta, precision, min_votes, select_factor, sig_floor, mag_tol, max_iters,
+                  max_batch, trace, profile, graph)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             check(lib.sfft4_plan(ctypes.byref(h), N, K, l, q, seed, ctypes.byref(o)), "sfft4_plan")
@@ -190,3 +206,97 @@ class Plan:
               "sfft4_trace_get")
         n = nf.value
         return y, f[:n], v[:n], vt[:n]
+
+
+class BatchPlan:
+    """Plan of a batch of signals of different sizes N_i and sparsities K_i, executed together
+    (each signal follows its own static schedule, Section 3.1; signal i uses Philox counter
+    (i, m, 0, 0)).  Outputs are rows of length Kmax = max K_i."""
+
+    def __init__(self, Ns, Ks, l=16, q=1.0, seed=0, *, B1=0, delta=1e-8, precision="fp32",
+                 min_votes=0, select_factor=2.0, sig_floor=1e-10, mag_tol=0.5, max_iters=64,
+                 profile=False, graph=False, device=None):
+        import torch
+        lib = _lib.load()
+        self.device = _device(device)
+        Ns = [int(n) for n in Ns]
+        Ks = [int(k) for k in Ks]
+        if len(Ns) != len(Ks) or not Ns:
+            raise ValueError("Ns and Ks must be non-empty and of equal length")
+        o = _opts(B1, delta, precision, min_votes, select_factor, sig_floor, mag_tol, max_iters,
+                  1, False, profile, graph)
+        nsig = len(Ns)
+        Na = (ctypes.c_int64 * nsig)(*Ns)
+        Ka = (ctypes.c_int64 * nsig)(*Ks)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(lib.sfft4_plan_batched(ctypes.byref(h), nsig, Na, Ka, l, q, seed, ctypes.byref(o)),
+                  "sfft4_plan_batched")
+        self._h = h
+        self.Ns, self.Ks, self.l, self.q, self.seed = Ns, Ks, l, q, seed
+        inf = _lib.BatchInfo()
+        check(lib.sfft4_get_batch_info(h, ctypes.byref(inf)), "sfft4_get_batch_info")
+        self.info = {k: getattr(inf, k) for k, _ in _lib.BatchInfo._fields_}
+        self.Kmax = self.info["Kmax"]
+        self._ptrs = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.load().sfft4_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def sync_status(self):
+        check(_lib.load().sfft4_sync_status(self._h), "sfft4_sync_status")
+
+    def profile(self, reset=True):
+        pr = _lib.Profile()
+        check(_lib.load().sfft4_profile_get(self._h, ctypes.byref(pr), int(bool(reset))), "sfft4_profile_get")
+        return {k: getattr(pr, k) for k, _ in _lib.Profile._fields_}
+
+    def outputs(self):
+        import torch
+        n, K, dev = len(self.Ns), self.Kmax, self.device
+        return (torch.empty((n, K), dtype=torch.int64, device=dev),
+                torch.empty((n, K), dtype=torch.complex128, device=dev),
+                torch.empty((n,), dtype=torch.int64, device=dev),
+                torch.empty((n, K), dtype=torch.int8, device=dev))
+
+    def pointers(self, xs):
+        """Device array of the signals' base addresses (reused across calls: the kernels read
+        it, so a captured graph sees new entries)."""
+        import torch
+        if len(xs) != len(self.Ns):
+            raise ValueError(f"expected {len(self.Ns)} signals")
+        for x, N in zip(xs, self.Ns):
+            if (not isinstance(x, torch.Tensor) or x.device.type != "cuda" or x.dtype != torch.complex64
+                    or x.dim() != 1 or x.shape[0] != N or x.stride(0) != 1):
+                raise ValueError(f"each signal must be a contiguous CUDA complex64 tensor of its N ({N})")
+        host = torch.tensor([x.data_ptr() for x in xs], dtype=torch.int64)
+        if self._ptrs is None:
+            self._ptrs = torch.empty(len(xs), dtype=torch.int64, device=self.device)
+        self._ptrs.copy_(host, non_blocking=False)
+        return self._ptrs
+
+    def execute(self, xs, out=None, ptrs=None):
+        """Transforms of the signals xs (list of CUDA complex64 tensors, xs[i] of length N_i).
+        Returns (idx, val, nfound, votes), rows of length Kmax; row i past K_i holds -1 / 0."""
+        if ptrs is None:
+            ptrs = self.pointers(xs)
+        idx, val, nf, votes = out if out is not None else self.outputs()
+        check(_lib.load().sfft4_execute_batched_v(self._h, ctypes.c_void_p(ptrs.data_ptr()),
+                                                  ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(val.data_ptr()),
+                                                  ctypes.c_void_p(nf.data_ptr()), ctypes.c_void_p(votes.data_ptr()),
+                                                  _stream_ptr(self.device)), "sfft4_execute_batched_v")
+        return idx, val, nf, votes

@@ -23,7 +23,7 @@ class Opts(ctypes.Structure):
                 ("sig_floor", ctypes.c_double), ("mag_tol", ctypes.c_double),
                 ("max_iters", ctypes.c_int32), ("max_batch", ctypes.c_int32),
                 ("trace", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("l2_fetch_bytes", ctypes.c_int32)]
+                ("l2_fetch_bytes", ctypes.c_int32), ("graph", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -32,6 +32,12 @@ class PlanInfo(ctypes.Structure):
                 ("max_R", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("samples_per_transform", ctypes.c_int64), ("found_capacity", ctypes.c_int64),
                 ("kernels_per_execute", ctypes.c_int32)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("nsig", ctypes.c_int32), ("n_classes", ctypes.c_int32), ("n_levels", ctypes.c_int32),
+                ("kernels_per_execute", ctypes.c_int32), ("Kmax", ctypes.c_int64),
+                ("samples_per_execute", ctypes.c_int64), ("precision", ctypes.c_int32)]
 
 
 class IterInfo(ctypes.Structure):
@@ -62,6 +68,11 @@ SIGNATURES = [
     ("sfft4_destroy", None, [_P]),
     ("sfft4_execute", ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     ("sfft4_execute_batched", ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, _P, _P, _P, _P, _P]),
+    ("sfft4_plan_batched", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                                          ctypes.POINTER(ctypes.c_int64), ctypes.c_int32, ctypes.c_double,
+                                          ctypes.c_uint64, ctypes.POINTER(Opts)]),
+    ("sfft4_execute_batched_v", ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    ("sfft4_get_batch_info", ctypes.c_int, [_P, ctypes.POINTER(BatchInfo)]),
     ("sfft4_get_plan_info", ctypes.c_int, [_P, ctypes.POINTER(PlanInfo)]),
     ("sfft4_get_iter_info", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(IterInfo)]),
     ("sfft4_get_window", ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),

@@ -100,6 +100,8 @@ struct DftArgs {
     const unsigned char* A;  // three bf16 pieces in core-matrix layout
     const float2* tw4;     // stage 2 twiddles (B entries)
     int32_t* status;       // set to 1 if a bounded wait gave up
+    const float2* const* in_cols;  // optional per-column input base pointers (else strides)
+    float2* const* out_cols;       // optional per-column output base pointers
     int B, B1, B2, R, P, copies, stage;  // stage 0: single (P = B); 1: four-step first; 2: second
     int64_t nvec, ngcols;
 };
@@ -158,8 +160,8 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_dft_bf16x3(const DftArgs a) 
                 float2 val[8];
                 if (g0 + n < a.ngcols && v < a.nvec) {
                     if (a.stage == 0) {
-                        const int64_t base = (v / R) * a.in_stride + (v % R) * B + e0;
-                        const float4* src = (const float4*)(a.in + base);
+                        const float2* cb = a.in_cols ? a.in_cols[v] : a.in + (v / R) * a.in_stride + (v % R) * B;
+                        const float4* src = (const float4*)(cb + e0);
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             const float4 f = src[q];
@@ -169,14 +171,14 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_dft_bf16x3(const DftArgs a) 
                     } else if (a.stage == 1) {
                         const int64_t col = v / B2;
                         const int j2 = (int)(v - col * B2);
-                        const int64_t base = (col / R) * a.in_stride + (col % R) * B + j2;
+                        const float2* cb = a.in_cols ? a.in_cols[col] : a.in + (col / R) * a.in_stride + (col % R) * B;
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) val[q] = a.in[base + (int64_t)B2 * (e0 + q)];
+                        for (int q = 0; q < 8; ++q) val[q] = cb[j2 + (int64_t)B2 * (e0 + q)];
                     } else {
                         const int64_t col = v / B1;
                         const int k1 = (int)(v - col * B1);
-                        const int64_t base = (col / R) * a.in_stride + (col % R) * B + (int64_t)k1 * B2 + e0;
-                        const float4* src = (const float4*)(a.in + base);
+                        const float2* cb = a.in_cols ? a.in_cols[col] : a.in + (col / R) * a.in_stride + (col % R) * B;
+                        const float4* src = (const float4*)(cb + (int64_t)k1 * B2 + e0);
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             const float4 f = src[q];
@@ -299,7 +301,8 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_dft_bf16x3(const DftArgs a) 
                 const int k1 = (int)(v - col * B1);
                 off = k1 + (int64_t)B1 * k;
             }
-            a.out[(col / R) * a.out_stride + (col % R) * B + off] = val;
+            float2* ob = a.out_cols ? a.out_cols[col] : a.out + (col / R) * a.out_stride + (col % R) * B;
+            ob[off] = val;
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
@@ -341,7 +344,8 @@ int configure_dft_tc() {
 // y_stride), through the scratch u (same layout as z) for the four-step case.
 int launch_dft_tc(const float2* z, int64_t z_stride, float2* u, float2* y, int64_t y_stride, int nsig,
                   int R, int B, const unsigned char* A1, const unsigned char* A2, const float2* tw4,
-                  int32_t* status, int sm_count, cudaStream_t st) {
+                  int32_t* status, int sm_count, cudaStream_t st, const float2* const* zcols,
+                  float2* const* ucols, float2* const* ycols, int64_t ncols_override) {
     int B1, B2;
     dft_factor(B, &B1, &B2);
     DftArgs a;
@@ -351,10 +355,12 @@ int launch_dft_tc(const float2* z, int64_t z_stride, float2* u, float2* y, int64
     a.B1 = B1;
     a.B2 = B2;
     a.R = R;
-    const int64_t ncols = (int64_t)nsig * R;
+    const int64_t ncols = ncols_override > 0 ? ncols_override : (int64_t)nsig * R;
     auto run = [&](int stage, const float2* in, int64_t is, float2* out, int64_t os, int P,
-                   const unsigned char* A, int64_t nvec) {
+                   const unsigned char* A, int64_t nvec, const float2* const* icols, float2* const* ocols) {
         a.stage = stage;
+        a.in_cols = icols;
+        a.out_cols = ocols;
         a.in = in;
         a.in_stride = is;
         a.out = out;
@@ -369,10 +375,10 @@ int launch_dft_tc(const float2* z, int64_t z_stride, float2* u, float2* y, int64
         k_dft_bf16x3<<<grid, kDftThreads, kDftSmem, st>>>(a);
         return check_cuda(cudaGetLastError());
     };
-    if (B2 == 1) return run(0, z, z_stride, y, y_stride, B, A1, ncols);
-    int rc = run(1, z, z_stride, u, z_stride, B1, A1, ncols * B2);
+    if (B2 == 1) return run(0, z, z_stride, y, y_stride, B, A1, ncols, zcols, ycols);
+    int rc = run(1, z, z_stride, u, z_stride, B1, A1, ncols * B2, zcols, ucols);
     if (rc) return rc;
-    return run(2, u, z_stride, y, y_stride, B2, A2, ncols * B1);
+    return run(2, u, z_stride, y, y_stride, B2, A2, ncols * B1, (const float2* const*)ucols, ycols);
 }
 
 }  // namespace sfft4

@@ -1,0 +1,369 @@
+// Batched sFFT4.0 over signals of different sizes N_i and sparsities K_i in one pass of
+// table-driven kernels.
+//
+// Signals with equal (N, K) share one static schedule ("class", Section 3.1); window tables
+// are shared by (N, B).  Execution is level-synchronous: level m runs iteration m of every
+// signal whose schedule has one.  Each level is a handful of launches whose CTAs take their
+// work from device tables built here: fold tiles (signal, fold group, residue slice), DFT
+// columns grouped by bucket count, decode jobs grouped by round count.  A whole execute can be
+// captured as one CUDA graph (opts.graph).
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <new>
+
+#include "sfft4_internal.cuh"
+
+namespace sfft4 {
+
+struct GroupLevel {
+    struct Fold {
+        int RG;
+        int64_t off;
+        int n, threads;
+        size_t smem;
+        int64_t samples;
+    };
+    struct Dft {
+        int B;
+        int64_t off;
+        int n;
+        Window w;
+    };
+    struct Dec {
+        int rclass;
+        int64_t off;
+        int n;
+        size_t smem;
+    };
+    std::vector<Fold> folds;
+    std::vector<Dft> dfts;
+    std::vector<Dec> decs;
+};
+
+struct Group {
+    int nsig = 0;
+    int64_t Kmax = 0;
+    std::vector<sfft4_plan_s*> cls;    // one schedule per distinct (N, K)
+    std::vector<int> slot_cls;
+    std::vector<Window> wcache;        // tables shared by (N, B), owned here
+    std::vector<GroupLevel> levels;
+    // device tables
+    FoldArgs* fold_jobs = nullptr;
+    FoldTile* tiles = nullptr;
+    const float2** zcols = nullptr;
+    float2** ucols = nullptr;
+    float2** ycols = nullptr;
+    DecodeArgs* dec_jobs = nullptr;
+    int32_t* dec_list = nullptr;
+    FinalJob* fin_jobs = nullptr;
+    // workspace
+    void* arena = nullptr;
+    int32_t* F = nullptr;
+    int32_t* hkeys = nullptr;
+    size_t hkeys_count = 0;
+    int64_t samples = 0;
+    int kernels = 0;
+};
+
+namespace {
+
+void free_group(Group* g) {
+    if (!g) return;
+    for (sfft4_plan_s* c : g->cls) {
+        cudaFree(c->iters_dev);
+        delete c;
+    }
+    for (auto& w : g->wcache) {
+        cudaFree(w.G);
+        cudaFree(w.Ghat);
+        cudaFree(w.tw);
+        cudaFree(w.dA1);
+        cudaFree(w.dA2);
+        cudaFree(w.tw4);
+    }
+    void* bufs[] = {g->fold_jobs, g->tiles, g->zcols, g->ucols, g->ycols, g->dec_jobs,
+                    g->dec_list, g->fin_jobs, g->arena};
+    for (void* b : bufs) cudaFree(b);
+    delete g;
+}
+
+template <class T>
+int upload(T** dst, const std::vector<T>& v) {
+    if (v.empty()) return SFFT4_OK;
+    int rc = check_cuda(cudaMalloc(dst, v.size() * sizeof(T)));
+    if (rc) return rc;
+    return check_cuda(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+
+void destroy_group(Group* g) { free_group(g); }
+
+int build_group_plan(sfft4_plan_s* p, int nsig, const int64_t* Ns, const int64_t* Ks, int32_t l,
+                     double q, uint64_t seed, const sfft4_opts* opts) {
+    Group* g = new (std::nothrow) Group();
+    if (!g) return SFFT4_ENOMEM;
+    p->grp = g;
+    g->nsig = nsig;
+    // classes of equal (N, K), each with its own static schedule
+    std::map<std::pair<int64_t, int64_t>, int> cls_of;
+    for (int i = 0; i < nsig; ++i) {
+        auto key = std::make_pair(Ns[i], Ks[i]);
+        auto itc = cls_of.find(key);
+        if (itc == cls_of.end()) {
+            sfft4_opts o;
+            int qn = 0;
+            int rc = plan_options(Ns[i], Ks[i], l, q, opts, &o, &qn);
+            if (rc) return rc;
+            sfft4_plan_s* c = new (std::nothrow) sfft4_plan_s();
+            if (!c) return SFFT4_ENOMEM;
+            g->cls.push_back(c);
+            c->N = Ns[i];
+            c->n = 0;
+            while ((int64_t(1) << c->n) < c->N) ++c->n;
+            c->K = Ks[i];
+            c->l = l;
+            c->qn = qn;
+            c->seed = seed;
+            c->o = o;
+            c->device = p->device;
+            rc = plan_schedule(c);
+            if (!rc) rc = plan_tables(c, &g->wcache);
+            if (rc) return rc;
+            itc = cls_of.emplace(key, (int)g->cls.size() - 1).first;
+        }
+        g->slot_cls.push_back(itc->second);
+        g->Kmax = std::max<int64_t>(g->Kmax, Ks[i]);
+    }
+    // workspace arena: per signal z, y, (u), found set, hash; per-signal scalars
+    struct Slot {
+        size_t z, y, u, ff, fv, fvt, hk, hv;
+    };
+    std::vector<Slot> so(nsig);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
+    const size_t oF = take((size_t)nsig * 4), oTh = take((size_t)nsig * 4), oFx = take((size_t)nsig * 4);
+    size_t hk_total = 0;
+    for (int i = 0; i < nsig; ++i) hk_total += (size_t)1 << g->cls[g->slot_cls[i]]->Hlog;
+    const size_t oHK = take(hk_total * 4);  // all hash keys contiguous (one reset memset)
+    size_t hk_run = 0;
+    for (int i = 0; i < nsig; ++i) {
+        const sfft4_plan_s* c = g->cls[g->slot_cls[i]];
+        const size_t rb = (size_t)c->R_max * c->B_max * sizeof(float2);
+        so[i].z = take(rb);
+        so[i].y = take(rb);
+        so[i].u = (p->o.precision == SFFT4_BF16X3) ? take(rb) : 0;
+        so[i].ff = take((size_t)c->Fcap * 4);
+        so[i].fv = take((size_t)c->Fcap * 16);
+        so[i].fvt = take((size_t)c->Fcap);
+        so[i].hk = oHK + hk_run * 4;
+        hk_run += (size_t)1 << c->Hlog;
+        so[i].hv = take(((size_t)1 << c->Hlog) * 4);
+    }
+    int rc = check_cuda(cudaMalloc(&g->arena, off));
+    if (rc) return rc;
+    char* A = (char*)g->arena;
+    g->F = (int32_t*)(A + oF);
+    float* theta = (float*)(A + oTh);
+    int32_t* fx = (int32_t*)(A + oFx);
+    g->hkeys = (int32_t*)(A + oHK);
+    g->hkeys_count = hk_total;
+
+    // level tables
+    int Mmax = 0;
+    for (sfft4_plan_s* c : g->cls) Mmax = std::max<int>(Mmax, (int)c->iters.size());
+    std::vector<FoldArgs> fjobs;
+    std::vector<FoldTile> tiles;
+    std::vector<const float2*> zc;
+    std::vector<float2*> uc, yc;
+    std::vector<DecodeArgs> djobs;
+    std::vector<int32_t> dlist;
+    for (int mi = 0; mi < Mmax; ++mi) {
+        GroupLevel L;
+        // fold tiles by round count of the group (register accumulators)
+        for (int RG = 1; RG <= kFoldRG; ++RG) {
+            GroupLevel::Fold f{RG, (int64_t)tiles.size(), 0, 0, 0, 0};
+            for (int i = 0; i < nsig; ++i) {
+                const sfft4_plan_s* c = g->cls[g->slot_cls[i]];
+                if (mi >= (int)c->iters.size()) continue;
+                const IterHost& ih = c->iters[mi];
+                for (const FoldGroup& fg : ih.groups) {
+                    if (fg.nr != RG) continue;
+                    size_t smem = 0;
+                    FoldArgs a = make_fold_args(c, mi, fg, &smem);
+                    a.z = (float2*)(A + so[i].z);
+                    a.signal0 = i;
+                    const int job = (int)fjobs.size();
+                    fjobs.push_back(a);
+                    for (int sl = 0; sl < ih.d.B / ih.Wj; ++sl) tiles.push_back({job, sl});
+                    f.threads = std::max(f.threads, ih.Wj * fg.P);
+                    f.smem = std::max(f.smem, smem);
+                    f.samples += fg.unique;
+                }
+            }
+            f.n = (int)((int64_t)tiles.size() - f.off);
+            if (f.n > 0) L.folds.push_back(f);
+        }
+        // DFT columns by bucket count
+        std::map<int, std::vector<int>> byB;
+        for (int i = 0; i < nsig; ++i) {
+            const sfft4_plan_s* c = g->cls[g->slot_cls[i]];
+            if (mi < (int)c->iters.size()) byB[c->iters[mi].d.B].push_back(i);
+        }
+        for (auto& kv : byB) {
+            GroupLevel::Dft d{kv.first, (int64_t)zc.size(), 0, Window()};
+            for (int i : kv.second) {
+                const sfft4_plan_s* c = g->cls[g->slot_cls[i]];
+                const IterHost& ih = c->iters[mi];
+                d.w = c->wins[ih.win];
+                for (int r = 0; r < ih.d.R; ++r) {
+                    zc.push_back((const float2*)(A + so[i].z) + (int64_t)r * ih.d.B);
+                    uc.push_back(so[i].u ? (float2*)(A + so[i].u) + (int64_t)r * ih.d.B : nullptr);
+                    yc.push_back((float2*)(A + so[i].y) + (int64_t)r * ih.d.B);
+                }
+            }
+            d.n = (int)((int64_t)zc.size() - d.off);
+            L.dfts.push_back(d);
+        }
+        // decode jobs by round class
+        for (int rcl = 0; rcl < 3; ++rcl) {
+            GroupLevel::Dec d{rcl, (int64_t)dlist.size(), 0, 0};
+            for (int i = 0; i < nsig; ++i) {
+                const sfft4_plan_s* c = g->cls[g->slot_cls[i]];
+                if (mi >= (int)c->iters.size()) continue;
+                const IterDev& id = c->iters[mi].d;
+                const int cl = id.R <= 8 ? 0 : (id.R <= 16 ? 1 : 2);
+                if (cl != rcl) continue;
+                DecodeArgs a = make_decode_args(c, mi);
+                a.signal0 = i;
+                a.y = (float2*)(A + so[i].y);
+                a.F = g->F + i;
+                a.ff = (int32_t*)(A + so[i].ff);
+                a.fv = (double2*)(A + so[i].fv);
+                a.fvotes = (int8_t*)(A + so[i].fvt);
+                a.hkeys = (int32_t*)(A + so[i].hk);
+                a.hvals = (int32_t*)(A + so[i].hv);
+                a.theta = theta + i;
+                a.fxexp = fx + i;
+                dlist.push_back((int32_t)djobs.size());
+                djobs.push_back(a);
+                d.smem = std::max(d.smem, decode_smem_bytes(id.B));
+            }
+            d.n = (int)((int64_t)dlist.size() - d.off);
+            if (d.n > 0) L.decs.push_back(d);
+        }
+        g->kernels += (int)(L.folds.size() + L.decs.size());
+        for (auto& d : L.dfts) g->kernels += (p->o.precision == SFFT4_BF16X3 && d.B > 64) ? 2 : 1;
+        g->levels.push_back(L);
+    }
+    g->kernels += 1;  // finalize
+    std::vector<FinalJob> fin(nsig);
+    for (int i = 0; i < nsig; ++i) {
+        const sfft4_plan_s* c = g->cls[g->slot_cls[i]];
+        fin[i] = FinalJob{g->F + i, (const int32_t*)(A + so[i].ff), (const double2*)(A + so[i].fv),
+                          (const int8_t*)(A + so[i].fvt), c->Fcap, c->K};
+        g->samples += c->samples;
+    }
+    rc = upload(&g->fold_jobs, fjobs);
+    if (!rc) rc = upload(&g->tiles, tiles);
+    if (!rc) rc = upload(&g->zcols, zc);
+    if (!rc) rc = upload(&g->ucols, uc);
+    if (!rc) rc = upload(&g->ycols, yc);
+    if (!rc) rc = upload(&g->dec_jobs, djobs);
+    if (!rc) rc = upload(&g->dec_list, dlist);
+    if (!rc) rc = upload(&g->fin_jobs, fin);
+    return rc;
+}
+
+namespace {
+struct GroupRun {
+    const float2* const* x;
+    int64_t* idx;
+    sfft4_c128* val;
+    int64_t* nfound;
+    int8_t* votes;
+};
+
+int group_body(sfft4_plan_s* p, const void* ctx, cudaStream_t st) {
+    const GroupRun& r = *(const GroupRun*)ctx;
+    Group* g = p->grp;
+    int rc = check_cuda(cudaMemsetAsync(g->F, 0, (size_t)g->nsig * sizeof(int32_t), st));
+    if (!rc) rc = check_cuda(cudaMemsetAsync(g->hkeys, 0xff, g->hkeys_count * sizeof(int32_t), st));
+    if (rc) return rc;
+    for (const GroupLevel& L : g->levels) {
+        for (const auto& f : L.folds) {
+            cudaEvent_t ev = nullptr;
+            rc = prof_begin(p, st, &ev);
+            if (!rc) rc = launch_fold_multi(f.RG, g->fold_jobs, g->tiles + f.off, f.n, r.x, f.threads, f.smem, st);
+            if (!rc) rc = prof_end(p, st, ev, kProfFold, f.samples);
+            if (rc) return rc;
+        }
+        for (const auto& d : L.dfts) {
+            cudaEvent_t ev = nullptr;
+            rc = prof_begin(p, st, &ev);
+            if (rc) return rc;
+            if (p->o.precision == SFFT4_BF16X3)
+                rc = launch_dft_tc(nullptr, 0, nullptr, nullptr, 0, 0, 1, d.B, d.w.dA1, d.w.dA2, d.w.tw4,
+                                   p->status, p->sm_count, st, g->zcols + d.off, g->ucols + d.off,
+                                   g->ycols + d.off, d.n);
+            else
+                rc = launch_fft_multi(g->zcols + d.off, g->ycols + d.off, d.n, d.B, d.w.tw, st);
+            if (!rc) rc = prof_end(p, st, ev, kProfFft, 0);
+            if (rc) return rc;
+        }
+        for (const auto& d : L.decs) {
+            cudaEvent_t ev = nullptr;
+            rc = prof_begin(p, st, &ev);
+            if (!rc) rc = launch_decode_multi(d.rclass, g->dec_jobs, g->dec_list + d.off, d.n, d.smem, st);
+            if (!rc) rc = prof_end(p, st, ev, kProfDecode, 0);
+            if (rc) return rc;
+        }
+    }
+    cudaEvent_t ev = nullptr;
+    rc = prof_begin(p, st, &ev);
+    if (!rc) rc = launch_finalize_multi(g->fin_jobs, g->nsig, g->Kmax, r.idx, r.val, r.nfound, r.votes, st);
+    if (!rc) rc = prof_end(p, st, ev, kProfFinalize, 0);
+    return rc;
+}
+}  // namespace
+
+}  // namespace sfft4
+
+using namespace sfft4;
+
+extern "C" {
+
+int sfft4_execute_batched_v(sfft4_plan_t p, const void* const* x_ptrs_dev, int64_t* idx_dev,
+                            sfft4_c128* val_dev, int64_t* nfound_dev, int8_t* votes_dev, void* stream) {
+    if (!p || !x_ptrs_dev || !idx_dev || !val_dev || !nfound_dev) return SFFT4_EINVAL;
+    if (!p->grp) return SFFT4_ESTATE;
+    const GroupRun r{(const float2* const*)x_ptrs_dev, idx_dev, val_dev, nfound_dev, votes_dev};
+    const uint64_t key[8] = {2, (uint64_t)(uintptr_t)x_ptrs_dev, (uint64_t)(uintptr_t)idx_dev,
+                             (uint64_t)(uintptr_t)val_dev, (uint64_t)(uintptr_t)nfound_dev,
+                             (uint64_t)(uintptr_t)votes_dev, 0, 0};
+    int rc = graph_run(p, key, (cudaStream_t)stream, group_body, &r);
+    if (!rc) p->executed = true;
+    return rc;
+}
+
+int sfft4_get_batch_info(sfft4_plan_t p, sfft4_batch_info* info) {
+    if (!p || !info) return SFFT4_EINVAL;
+    if (!p->grp) return SFFT4_ESTATE;
+    const Group* g = p->grp;
+    memset(info, 0, sizeof(*info));
+    info->nsig = g->nsig;
+    info->n_classes = (int32_t)g->cls.size();
+    info->n_levels = (int32_t)g->levels.size();
+    info->kernels_per_execute = g->kernels;
+    info->Kmax = g->Kmax;
+    info->samples_per_execute = g->samples;
+    info->precision = p->o.precision;
+    return SFFT4_OK;
+}
+
+}  // extern "C"

@@ -13,6 +13,7 @@
 // fixed point with order-independent integer atomics, so repeated runs are bit-identical.
 #include <math.h>
 #include <stdio.h>
+#include <string.h>
 
 #include <algorithm>
 
@@ -148,19 +149,6 @@ int build_window_tables(sfft4_plan_s* p, Window* w, double delta) {
 }
 
 // ----------------------------------------------------------------- fold -------------
-struct FoldArgs {
-    const float2* x;
-    int64_t x_stride;
-    float2* z;
-    int64_t z_stride;
-    uint64_t N, seed;
-    int32_t m, signal0, B, logB, Wj, h, w, Mrows;
-    const float* G;
-    FoldGroup g;
-    int32_t tau[kFoldRG];
-    int32_t mlo[kFoldRG];   // first multiple m' of B with rows of round s in shared memory
-    int32_t soff[kFoldRG];  // (s Mrows - mlo_s) Wj: shared-memory offset of round s
-};
 
 constexpr int kFoldUnroll = 4;
 
@@ -174,19 +162,18 @@ constexpr int kFoldUnroll = 4;
 // in 32 bits: N = 2^n divides 2^32, so (sigma t + a) mod N is the low n bits of the wrapped
 // 32-bit value.
 template <int RG>
-__global__ void __launch_bounds__(512, 2) k_fold(const FoldArgs a) {
-    extern __shared__ float gsm[];  // [RG][Mrows][Wj]
-    __shared__ uint32_t s_par[2];
-    __shared__ float2 red[512];
+__device__ __forceinline__ void fold_body(const FoldArgs& a, int slice, int64_t signal_index,
+                                          const float2* __restrict__ x, float2* zsig, float* gsm,
+                                          uint32_t* s_par, float2* red) {
     const int tid = threadIdx.x, T = blockDim.x;
     const int Wj = a.Wj, B = a.B, Mrows = a.Mrows;
     const int P = a.g.P;
+    const bool active = tid < Wj * P;  // a launch may carry more threads than this job uses
     const int jj = tid % Wj, p = tid / Wj;
-    const int sig = blockIdx.y;
-    const int rho0 = blockIdx.x * Wj;
+    const int rho0 = slice * Wj;
     if (tid == 0) {
         uint64_t s, o;
-        permutation_draw(a.seed, (uint64_t)(a.signal0 + sig), (uint64_t)a.m, a.N, &s, &o);
+        permutation_draw(a.seed, (uint64_t)signal_index, (uint64_t)a.m, a.N, &s, &o);
         s_par[0] = (uint32_t)s;
         s_par[1] = (uint32_t)o;
     }
@@ -204,12 +191,11 @@ __global__ void __launch_bounds__(512, 2) k_fold(const FoldArgs a) {
     const int PB = P * B;
     const int rho = rho0 + jj + p * B;  // residue mod P B
     const uint32_t step = sigma * (uint32_t)PB;
-    const float2* __restrict__ x = a.x + (int64_t)sig * a.x_stride;
     float2 acc[RG];
 #pragma unroll
     for (int s = 0; s < RG; ++s) acc[s] = make_float2(0.f, 0.f);
 
-    for (int sg = 0; sg < a.g.nseg; ++sg) {
+    for (int sg = 0; active && sg < a.g.nseg; ++sg) {
         const int t0 = (int)a.g.t0[sg], t1 = (int)a.g.t1[sg];
         const uint32_t rm = a.g.mask[sg];
         int d = (rho - t0) % PB;
@@ -249,7 +235,7 @@ __global__ void __launch_bounds__(512, 2) k_fold(const FoldArgs a) {
         if (s < a.g.nr) {
             red[tid] = acc[s];
             __syncthreads();
-            if (p == 0) {
+            if (p == 0 && active) {
                 float2 sum = red[jj];
                 for (int pp = 1; pp < P; ++pp) {
                     float2 o = red[jj + pp * Wj];
@@ -258,11 +244,40 @@ __global__ void __launch_bounds__(512, 2) k_fold(const FoldArgs a) {
                 }
                 int slot = (rho0 + jj - a.tau[s]) % B;
                 if (slot < 0) slot += B;
-                a.z[(int64_t)sig * a.z_stride + (int64_t)(a.g.r0 + s) * B + slot] = sum;
+                if (active) zsig[(int64_t)(a.g.r0 + s) * B + slot] = sum;
             }
             __syncthreads();
         }
     }
+}
+
+template <int RG>
+__global__ void __launch_bounds__(512, 2) k_fold(const FoldArgs a) {
+    extern __shared__ float gsm[];  // [RG][Mrows][Wj]
+    __shared__ uint32_t s_par[2];
+    __shared__ float2 red[512];
+    const int sig = blockIdx.y;
+    fold_body<RG>(a, blockIdx.x, (int64_t)a.signal0 + sig, a.x + (int64_t)sig * a.x_stride,
+                  a.z + (int64_t)sig * a.z_stride, gsm, s_par, red);
+}
+
+// Tile queue of a batch of signals with different N and K: CTA b takes tile tiles[b] = (job,
+// residue slice) of one level; the job (a FoldArgs with the signal's own z block in z and its
+// batch index in signal0) is copied to shared memory first.  x of signal s is xptrs[s].
+
+template <int RG>
+__global__ void __launch_bounds__(512, 2) k_fold_multi(const FoldArgs* __restrict__ jobs,
+                                                       const FoldTile* __restrict__ tiles,
+                                                       const float2* const* __restrict__ xptrs) {
+    extern __shared__ float gsm[];
+    __shared__ uint32_t s_par[2];
+    __shared__ float2 red[512];
+    __shared__ __align__(16) FoldArgs sa;
+    const FoldTile t = tiles[blockIdx.x];
+    for (int i = threadIdx.x; i < (int)(sizeof(FoldArgs) / 4); i += blockDim.x)
+        ((uint32_t*)&sa)[i] = ((const uint32_t*)(jobs + t.job))[i];
+    __syncthreads();
+    fold_body<RG>(sa, t.slice, sa.signal0, xptrs[sa.signal0], sa.z, gsm, s_par, red);
 }
 
 // ----------------------------------------------------------------- FFT --------------
@@ -270,7 +285,7 @@ __global__ void __launch_bounds__(512, 2) k_fold(const FoldArgs a) {
 // `cpc` columns per CTA in shared memory; column c = signal * R + round.
 __global__ void k_fft(const float2* __restrict__ z, float2* __restrict__ y, int B, int logB,
                       const float2* __restrict__ tw, int64_t z_stride, int64_t y_stride, int R,
-                      int cpc, int ncols) {
+                      int cpc, int ncols, const float2* const* zcols, float2* const* ycols) {
     extern __shared__ float2 sm[];
     const int tid = threadIdx.x, T = blockDim.x;
     const int c0 = blockIdx.x * cpc;
@@ -278,8 +293,8 @@ __global__ void k_fft(const float2* __restrict__ z, float2* __restrict__ y, int 
     for (int i = tid; i < ncol * B; i += T) {
         int c = i >> logB, e = i & (B - 1);
         int col = c0 + c;
-        int64_t base = (int64_t)(col / R) * z_stride + (int64_t)(col % R) * B;
-        sm[c * B + (__brev((unsigned)e) >> (32 - logB))] = z[base + e];
+        const float2* zc = zcols ? zcols[col] : z + (int64_t)(col / R) * z_stride + (int64_t)(col % R) * B;
+        sm[c * B + (__brev((unsigned)e) >> (32 - logB))] = zc[e];
     }
     __syncthreads();
     for (int ls = 0; ls < logB; ++ls) {
@@ -299,8 +314,8 @@ __global__ void k_fft(const float2* __restrict__ z, float2* __restrict__ y, int 
     for (int i = tid; i < ncol * B; i += T) {
         int c = i >> logB, e = i & (B - 1);
         int col = c0 + c;
-        int64_t base = (int64_t)(col / R) * y_stride + (int64_t)(col % R) * B;
-        y[base + e] = sm[c * B + e];
+        float2* yc = ycols ? ycols[col] : y + (int64_t)(col / R) * y_stride + (int64_t)(col % R) * B;
+        yc[e] = sm[c * B + e];
     }
 }
 
@@ -384,24 +399,6 @@ __host__ __device__ inline size_t decode_smem(int B) {
     return base > upd ? base : upd;
 }
 
-struct DecodeArgs {
-    uint64_t N, seed;
-    int32_t n, signal0, first, l, qn, min_votes;
-    float mag_tol, sig_floor;
-    const IterDev* it;
-    float2* y;
-    int64_t y_stride;
-    int32_t* F;
-    int32_t* ff;
-    double2* fv;
-    int8_t* fvotes;
-    int64_t Fcap;
-    int32_t* hkeys;
-    int32_t* hvals;
-    int32_t Hlog;
-    float* theta;
-    int32_t* fxexp;
-};
 
 // Median of v[0..R-1] (R <= RMAX): mean of the two middle values for even R (Eq. 14
 // over rounds, reading R12).  RMAX = 16 sorts a fully unrolled bitonic network in registers
@@ -519,7 +516,7 @@ __device__ uint32_t block_radix_select(const float* key, int b_lo, int b_hi, int
 // All modular arithmetic is exact in 32 bits (N = 2^n divides 2^32).  RMAX bounds the
 // rounds R of the iteration (16, or 64 for extreme (l, q)).
 template <int RMAX>
-__global__ void __launch_bounds__(kDecodeThreads) k_decode(const DecodeArgs a) {
+__device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ uint32_t s_par[3];
     __shared__ int s_ws[33];
@@ -531,7 +528,6 @@ __global__ void __launch_bounds__(kDecodeThreads) k_decode(const DecodeArgs a) {
     __shared__ int s_fx;
     const IterDev* __restrict__ it = a.it;
     const int tid = threadIdx.x, T = blockDim.x;
-    const int sig = blockIdx.x;
     const int B = it->B, R = it->R, S = it->S, logL = it->logL;
     const uint32_t L = (uint32_t)it->L;
     const uint32_t N = (uint32_t)a.N, mask = N - 1, halfN = N >> 1;
@@ -822,19 +818,37 @@ __global__ void __launch_bounds__(kDecodeThreads) k_decode(const DecodeArgs a) {
     if (tid == 0) a.F[sig] = F0 + nnew;
 }
 
+template <int RMAX>
+__global__ void __launch_bounds__(kDecodeThreads) k_decode(const DecodeArgs a) {
+    decode_body<RMAX>(a, blockIdx.x);
+}
+
+// Batch of signals with different N and K: CTA b decodes signal jobs[list[b]], whose
+// DecodeArgs already point at that signal's own workspace (so it is signal 0 of its args).
+template <int RMAX>
+__global__ void __launch_bounds__(kDecodeThreads) k_decode_multi(const DecodeArgs* __restrict__ jobs,
+                                                                 const int32_t* __restrict__ list) {
+    __shared__ __align__(16) DecodeArgs sa;
+    const DecodeArgs* src = jobs + list[blockIdx.x];
+    for (int i = threadIdx.x; i < (int)(sizeof(DecodeArgs) / 4); i += blockDim.x)
+        ((uint32_t*)&sa)[i] = ((const uint32_t*)src)[i];
+    __syncthreads();
+    decode_body<RMAX>(sa, 0);
+}
+
 // ----------------------------------------------------------------- finalize ---------
 // Top-K of the found set by |v| (ties to the lower frequency), sorted by frequency.
-__global__ void __launch_bounds__(1024) k_finalize(const int32_t* Fc, const int32_t* ffa,
-                                                   const double2* fva, const int8_t* fvta,
-                                                   int64_t Fcap, int64_t K, int64_t* idx_out,
-                                                   sfft4_c128* val_out, int64_t* nfound_out,
-                                                   int8_t* votes_out) {
+__device__ __forceinline__ void finalize_body(const int32_t* Fc, const int32_t* ffa,
+                                              const double2* fva, const int8_t* fvta,
+                                              int64_t Fcap, int64_t K, int64_t Kout,
+                                              int64_t* idx_out, sfft4_c128* val_out,
+                                              int64_t* nfound_out, int8_t* votes_out,
+                                              const int sig, const int osig) {
     extern __shared__ __align__(16) unsigned char smraw[];
     unsigned long long* srt = (unsigned long long*)smraw;  // (f << 32 | entry), pow2 >= K
     __shared__ int s_cnt;
     __shared__ int s_ws[33];
     const int tid = threadIdx.x, T = blockDim.x;
-    const int sig = blockIdx.x;
     const int F0 = Fc[sig];
     const int32_t* ff = ffa + (int64_t)sig * Fcap;
     const double2* fv = fva + (int64_t)sig * Fcap;
@@ -900,8 +914,8 @@ __global__ void __launch_bounds__(1024) k_finalize(const int32_t* Fc, const int3
             __syncthreads();
         }
     }
-    for (int i = tid; i < K; i += T) {
-        const int64_t o = (int64_t)sig * K + i;
+    for (int i = tid; i < Kout; i += T) {
+        const int64_t o = (int64_t)osig * Kout + i;
         if (i < nsel) {
             const int e = (int)(srt[i] & 0xffffffffu);
             idx_out[o] = (int64_t)(srt[i] >> 32);
@@ -915,11 +929,62 @@ __global__ void __launch_bounds__(1024) k_finalize(const int32_t* Fc, const int3
             if (votes_out) votes_out[o] = 0;
         }
     }
-    if (tid == 0) nfound_out[sig] = nsel;
+    if (tid == 0) nfound_out[osig] = nsel;
+}
+
+__global__ void __launch_bounds__(1024) k_finalize(const int32_t* Fc, const int32_t* ffa,
+                                                   const double2* fva, const int8_t* fvta,
+                                                   int64_t Fcap, int64_t K, int64_t* idx_out,
+                                                   sfft4_c128* val_out, int64_t* nfound_out,
+                                                   int8_t* votes_out) {
+    finalize_body(Fc, ffa, fva, fvta, Fcap, K, K, idx_out, val_out, nfound_out, votes_out, blockIdx.x,
+                  blockIdx.x);
+}
+
+// Batch of signals with different K: job b finalises signal slot b (its found set at its own
+// workspace), writing row b of outputs of row length Kout (entries past the signal's K = -1).
+
+__global__ void __launch_bounds__(1024) k_finalize_multi(const FinalJob* __restrict__ jobs, int64_t Kout,
+                                                         int64_t* idx_out, sfft4_c128* val_out,
+                                                         int64_t* nfound_out, int8_t* votes_out) {
+    const FinalJob j = jobs[blockIdx.x];
+    finalize_body(j.F, j.ff, j.fv, j.fvt, j.Fcap, j.K, Kout, idx_out, val_out, nfound_out, votes_out, 0,
+                  blockIdx.x);
 }
 
 // ----------------------------------------------------------------- launchers --------
 int configure_kernels();
+
+FoldArgs make_fold_args(const sfft4_plan_s* p, int mi, const FoldGroup& g, size_t* smem_out) {
+    const IterHost& ih = p->iters[mi];
+    const IterDev& d = ih.d;
+    FoldArgs a;
+    memset(&a, 0, sizeof(a));
+    a.z_stride = (int64_t)p->R_max * p->B_max;
+    a.N = (uint64_t)p->N;
+    a.seed = p->seed;
+    a.m = d.m;
+    a.B = d.B;
+    a.logB = d.logB;
+    a.Wj = ih.Wj;
+    a.h = d.h;
+    a.w = 2 * d.h + 1;
+    a.G = d.G;
+    a.g = g;
+    // rows m' of B with tau_s - h <= rho + m' B <= tau_s + h for some rho in [0, B)
+    int Mrows = 0;
+    for (int s = 0; s < kFoldRG; ++s) {
+        a.tau[s] = (s < g.nr) ? (int32_t)d.tau[g.r0 + s] : 0;
+        int64_t lo = floor_div(a.tau[s] - (int64_t)d.h - (d.B - 1), d.B);
+        int64_t hi = floor_div(a.tau[s] + (int64_t)d.h, d.B);
+        a.mlo[s] = (int32_t)lo;
+        if (s < g.nr) Mrows = std::max<int>(Mrows, (int)(hi - lo + 1));
+    }
+    a.Mrows = Mrows;
+    for (int s = 0; s < kFoldRG; ++s) a.soff[s] = (s * Mrows - a.mlo[s]) * ih.Wj;
+    if (smem_out) *smem_out = (size_t)g.nr * Mrows * ih.Wj * sizeof(float);
+    return a;
+}
 
 int launch_bucketize(sfft4_plan_s* p, int mi, int nsig, const float2* x, int64_t x_stride,
                      int32_t signal0, float2* y_out, int64_t y_sig_stride, cudaStream_t st) {
@@ -928,36 +993,14 @@ int launch_bucketize(sfft4_plan_s* p, int mi, int nsig, const float2* x, int64_t
     const IterHost& ih = p->iters[mi];
     const IterDev& d = ih.d;
     for (const FoldGroup& g : ih.groups) {
-        FoldArgs a;
+        size_t smem = 0;
+        FoldArgs a = make_fold_args(p, mi, g, &smem);
         a.x = x;
         a.x_stride = x_stride;
         a.z = p->z;
-        a.z_stride = (int64_t)p->R_max * p->B_max;
-        a.N = (uint64_t)p->N;
-        a.seed = p->seed;
-        a.m = d.m;
         a.signal0 = signal0;
-        a.B = d.B;
-        a.logB = d.logB;
-        a.Wj = ih.Wj;
-        a.h = d.h;
-        a.w = 2 * d.h + 1;
-        a.G = d.G;
-        a.g = g;
-        // rows m' of B with tau_s - h <= rho + m' B <= tau_s + h for some rho in [0, B)
-        int Mrows = 0;
-        for (int s = 0; s < kFoldRG; ++s) {
-            a.tau[s] = (s < g.nr) ? (int32_t)d.tau[g.r0 + s] : 0;
-            int64_t lo = floor_div(a.tau[s] - (int64_t)d.h - (d.B - 1), d.B);
-            int64_t hi = floor_div(a.tau[s] + (int64_t)d.h, d.B);
-            a.mlo[s] = (int32_t)lo;
-            if (s < g.nr) Mrows = std::max<int>(Mrows, (int)(hi - lo + 1));
-        }
-        a.Mrows = Mrows;
-        for (int s = 0; s < kFoldRG; ++s) a.soff[s] = (s * Mrows - a.mlo[s]) * ih.Wj;
         dim3 grid(d.B / ih.Wj, nsig);
         int threads = ih.Wj * g.P;
-        size_t smem = (size_t)g.nr * Mrows * ih.Wj * sizeof(float);
         cudaEvent_t ev = nullptr;
         int rc = prof_begin(p, st, &ev);
         if (rc) return rc;
@@ -990,18 +1033,16 @@ int launch_bucketize(sfft4_plan_s* p, int mi, int nsig, const float2* x, int64_t
                            w.dA1, w.dA2, w.tw4, p->status, p->sm_count, st);
     } else {
         k_fft<<<blocks, T, smem, st>>>(p->z, y_out, B, logB, d.tw, (int64_t)p->R_max * p->B_max,
-                                       y_sig_stride, R, cpc, ncols);
+                                       y_sig_stride, R, cpc, ncols, nullptr, nullptr);
         rc = check_cuda(cudaGetLastError());
     }
     if (rc) return rc;
     return prof_end(p, st, ev, kProfFft, 0);
 }
 
-int launch_decode(sfft4_plan_s* p, int mi, int nsig, cudaStream_t st) {
-    int rc0 = configure_kernels();
-    if (rc0) return rc0;
-    const IterDev& d = p->iters[mi].d;
+DecodeArgs make_decode_args(const sfft4_plan_s* p, int mi) {
     DecodeArgs a;
+    memset(&a, 0, sizeof(a));
     a.N = (uint64_t)p->N;
     a.seed = p->seed;
     a.n = p->n;
@@ -1025,6 +1066,14 @@ int launch_decode(sfft4_plan_s* p, int mi, int nsig, cudaStream_t st) {
     a.Hlog = p->Hlog;
     a.theta = p->theta;
     a.fxexp = p->fxexp;
+    return a;
+}
+
+int launch_decode(sfft4_plan_s* p, int mi, int nsig, cudaStream_t st) {
+    int rc0 = configure_kernels();
+    if (rc0) return rc0;
+    const IterDev& d = p->iters[mi].d;
+    DecodeArgs a = make_decode_args(p, mi);
     size_t smem = decode_smem(d.B);
     cudaEvent_t ev = nullptr;
     int rc = prof_begin(p, st, &ev);
@@ -1035,6 +1084,53 @@ int launch_decode(sfft4_plan_s* p, int mi, int nsig, cudaStream_t st) {
     rc = check_cuda(cudaGetLastError());
     if (rc) return rc;
     return prof_end(p, st, ev, kProfDecode, 0);
+}
+
+size_t decode_smem_bytes(int B) { return decode_smem(B); }
+
+// ---- launches of a batch of signals with different sizes (job tables in device memory) --
+int launch_fold_multi(int RG, const FoldArgs* jobs, const FoldTile* tiles, int ntiles,
+                      const float2* const* xptrs, int threads, size_t smem, cudaStream_t st) {
+    switch (RG) {
+        case 1: k_fold_multi<1><<<ntiles, threads, smem, st>>>(jobs, tiles, xptrs); break;
+        case 2: k_fold_multi<2><<<ntiles, threads, smem, st>>>(jobs, tiles, xptrs); break;
+        case 3: k_fold_multi<3><<<ntiles, threads, smem, st>>>(jobs, tiles, xptrs); break;
+        case 4: k_fold_multi<4><<<ntiles, threads, smem, st>>>(jobs, tiles, xptrs); break;
+        case 5: k_fold_multi<5><<<ntiles, threads, smem, st>>>(jobs, tiles, xptrs); break;
+        case 6: k_fold_multi<6><<<ntiles, threads, smem, st>>>(jobs, tiles, xptrs); break;
+        case 7: k_fold_multi<7><<<ntiles, threads, smem, st>>>(jobs, tiles, xptrs); break;
+        default: k_fold_multi<8><<<ntiles, threads, smem, st>>>(jobs, tiles, xptrs); break;
+    }
+    return check_cuda(cudaGetLastError());
+}
+
+int launch_fft_multi(const float2* const* zcols, float2* const* ycols, int ncols, int B,
+                     const float2* tw, cudaStream_t st) {
+    int logB = 0;
+    while ((1 << logB) < B) ++logB;
+    int T = std::min(1024, std::max(256, B / 2));
+    int cpc = std::max(1, (2 * T) / B);
+    int blocks = (ncols + cpc - 1) / cpc;
+    size_t smem = (size_t)cpc * B * sizeof(float2);
+    k_fft<<<blocks, T, smem, st>>>(nullptr, nullptr, B, logB, tw, 0, 0, 1, cpc, ncols, zcols, ycols);
+    return check_cuda(cudaGetLastError());
+}
+
+int launch_decode_multi(int rclass, const DecodeArgs* jobs, const int32_t* list, int n, size_t smem,
+                        cudaStream_t st) {
+    if (rclass == 0) k_decode_multi<8><<<n, kDecodeThreads, smem, st>>>(jobs, list);
+    else if (rclass == 1) k_decode_multi<16><<<n, kDecodeThreads, smem, st>>>(jobs, list);
+    else k_decode_multi<64><<<n, kDecodeThreads, smem, st>>>(jobs, list);
+    return check_cuda(cudaGetLastError());
+}
+
+int launch_finalize_multi(const FinalJob* jobs, int nsig, int64_t Kout, int64_t* idx, sfft4_c128* val,
+                          int64_t* nfound, int8_t* votes, cudaStream_t st) {
+    int P2 = 1;
+    while (P2 < Kout) P2 <<= 1;
+    size_t smem = (size_t)P2 * sizeof(unsigned long long);
+    k_finalize_multi<<<nsig, 1024, smem, st>>>(jobs, Kout, idx, val, nfound, votes);
+    return check_cuda(cudaGetLastError());
 }
 
 int launch_finalize(sfft4_plan_s* p, int nsig, int64_t* idx, sfft4_c128* val, int64_t* nfound,
@@ -1098,8 +1194,21 @@ int configure_kernels() {
     const void* folds[] = {(const void*)k_fold<1>, (const void*)k_fold<2>, (const void*)k_fold<3>,
                            (const void*)k_fold<4>, (const void*)k_fold<5>, (const void*)k_fold<6>,
                            (const void*)k_fold<7>, (const void*)k_fold<8>};
+    const void* folds_m[] = {(const void*)k_fold_multi<1>, (const void*)k_fold_multi<2>,
+                             (const void*)k_fold_multi<3>, (const void*)k_fold_multi<4>,
+                             (const void*)k_fold_multi<5>, (const void*)k_fold_multi<6>,
+                             (const void*)k_fold_multi<7>, (const void*)k_fold_multi<8>};
     for (const void* f : folds)
         if (!rc) rc = check_cuda(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kFoldSmemMax));
+    for (const void* f : folds_m)
+        if (!rc) rc = check_cuda(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kFoldSmemMax));
+    const void* decs_m[] = {(const void*)k_decode_multi<8>, (const void*)k_decode_multi<16>,
+                            (const void*)k_decode_multi<64>};
+    for (const void* f : decs_m)
+        if (!rc) rc = check_cuda(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)decode_smem(kBMax)));
+    if (!rc) rc = check_cuda(cudaFuncSetAttribute(k_finalize_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  8 * kKMax));
     if (!rc) rc = check_cuda(cudaFuncSetAttribute(k_decode<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   (int)decode_smem(kBMax)));
     if (!rc) rc = check_cuda(cudaFuncSetAttribute(k_decode<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1113,16 +1222,58 @@ int configure_kernels() {
     return rc;
 }
 
+int graph_run(sfft4_plan_s* p, const uint64_t key[8], cudaStream_t st,
+              int (*body)(sfft4_plan_s*, const void*, cudaStream_t), const void* ctx) {
+    int rc = configure_kernels();
+    if (rc) return rc;
+    if (!p->o.graph || p->o.profile || p->o.trace) return body(p, ctx, st);
+    if (p->gexec && memcmp(key, p->gkey, sizeof(p->gkey)) == 0) return check_cuda(cudaGraphLaunch(p->gexec, st));
+    if (p->gexec) {
+        rc = check_cuda(cudaGraphExecDestroy(p->gexec));
+        p->gexec = nullptr;
+        if (rc) return rc;
+    }
+    if (!p->gstream) {
+        rc = check_cuda(cudaStreamCreateWithFlags(&p->gstream, cudaStreamNonBlocking));
+        if (rc) return rc;
+    }
+    rc = check_cuda(cudaStreamBeginCapture(p->gstream, cudaStreamCaptureModeThreadLocal));
+    if (rc) return rc;
+    rc = body(p, ctx, p->gstream);
+    cudaGraph_t g = nullptr;
+    const int rc_end = check_cuda(cudaStreamEndCapture(p->gstream, &g));
+    if (!rc) rc = rc_end;
+    if (!rc) rc = check_cuda(cudaGraphInstantiate(&p->gexec, g, 0));
+    if (g) cudaGraphDestroy(g);
+    if (rc) {
+        p->gexec = nullptr;
+        return rc;
+    }
+    memcpy(p->gkey, key, sizeof(p->gkey));
+    return check_cuda(cudaGraphLaunch(p->gexec, st));
+}
+
 }  // namespace sfft4
 
 using namespace sfft4;
 
 namespace {
-int run(sfft4_plan_s* p, int nsig, const float2* x, int64_t x_stride, int64_t* idx,
-        sfft4_c128* val, int64_t* nfound, int8_t* votes, cudaStream_t st) {
-    int rc = configure_kernels();
-    if (rc) return rc;
-    rc = launch_reset(p, nsig, st);
+struct RunArgs {
+    int nsig;
+    const float2* x;
+    int64_t x_stride;
+    int64_t* idx;
+    sfft4_c128* val;
+    int64_t* nfound;
+    int8_t* votes;
+};
+
+int run_body(sfft4_plan_s* p, const void* ctx, cudaStream_t st) {
+    const RunArgs& r = *(const RunArgs*)ctx;
+    const int nsig = r.nsig;
+    const float2* x = r.x;
+    const int64_t x_stride = r.x_stride;
+    int rc = launch_reset(p, nsig, st);
     if (rc) return rc;
     const int64_t rb = (int64_t)p->R_max * p->B_max;
     for (size_t mi = 0; mi < p->iters.size(); ++mi) {
@@ -1147,7 +1298,17 @@ int run(sfft4_plan_s* p, int nsig, const float2* x, int64_t x_stride, int64_t* i
             if (rc) return rc;
         }
     }
-    rc = launch_finalize(p, nsig, idx, val, nfound, votes, st);
+    return launch_finalize(p, nsig, r.idx, r.val, r.nfound, r.votes, st);
+}
+
+int run(sfft4_plan_s* p, int nsig, const float2* x, int64_t x_stride, int64_t* idx,
+        sfft4_c128* val, int64_t* nfound, int8_t* votes, cudaStream_t st) {
+    if (p->grp) return SFFT4_ESTATE;
+    const RunArgs r{nsig, x, x_stride, idx, val, nfound, votes};
+    const uint64_t key[8] = {1, (uint64_t)nsig, (uint64_t)(uintptr_t)x, (uint64_t)x_stride,
+                             (uint64_t)(uintptr_t)idx, (uint64_t)(uintptr_t)val,
+                             (uint64_t)(uintptr_t)nfound, (uint64_t)(uintptr_t)votes};
+    int rc = graph_run(p, key, st, run_body, &r);
     if (!rc) p->executed = true;
     return rc;
 }
@@ -1166,6 +1327,7 @@ int sfft4_execute_batched(sfft4_plan_t p, int32_t nsig, const void* x_dev, int64
                           int64_t* idx_dev, sfft4_c128* val_dev, int64_t* nfound_dev,
                           int8_t* votes_dev, void* stream) {
     if (!p || !x_dev || !idx_dev || !val_dev || !nfound_dev) return SFFT4_EINVAL;
+    if (p->grp) return SFFT4_ESTATE;
     if (nsig < 1 || nsig > p->o.max_batch || x_stride < p->N) return SFFT4_EINVAL;
     return run(p, nsig, (const float2*)x_dev, x_stride, idx_dev, val_dev, nfound_dev, votes_dev,
                (cudaStream_t)stream);
@@ -1174,7 +1336,7 @@ int sfft4_execute_batched(sfft4_plan_t p, int32_t nsig, const void* x_dev, int64
 int sfft4_bucketize(sfft4_plan_t p, const void* x_dev, int32_t signal, int32_t m, void* y_dev,
                     void* stream) {
     if (!p || !x_dev || !y_dev || signal < 0 || m < 1 || m > (int32_t)p->iters.size())
-        return SFFT4_EINVAL;
+        return p && p->grp ? SFFT4_ESTATE : SFFT4_EINVAL;
     const IterDev& d = p->iters[m - 1].d;
     return launch_bucketize(p, m - 1, 1, (const float2*)x_dev, p->N, signal, (float2*)y_dev,
                             (int64_t)d.R * d.B, (cudaStream_t)stream);

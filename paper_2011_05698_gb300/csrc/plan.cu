@@ -114,19 +114,24 @@ void build_group(FoldGroup* g, const int64_t* tau, int r0, int nr, int64_t h) {
 
 void free_plan(sfft4_plan_s* p) {
     if (!p) return;
-    for (auto& w : p->wins) {
-        cudaFree(w.G);
-        cudaFree(w.Ghat);
-        cudaFree(w.tw);
-        cudaFree(w.dA1);
-        cudaFree(w.dA2);
-        cudaFree(w.tw4);
+    if (p->owns_tables) {
+        for (auto& w : p->wins) {
+            cudaFree(w.G);
+            cudaFree(w.Ghat);
+            cudaFree(w.tw);
+            cudaFree(w.dA1);
+            cudaFree(w.dA2);
+            cudaFree(w.tw4);
+        }
     }
     void* bufs[] = {p->iters_dev, p->z, p->y, p->u, p->status, p->F, p->ff, p->fv, p->fvotes, p->hkeys,
                     p->hvals, p->theta, p->fxexp, p->trace_y, p->trace_F, p->trace_ff,
                     p->trace_fv, p->trace_votes};
     for (void* b : bufs) cudaFree(b);
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->gstream) cudaStreamDestroy(p->gstream);
+    sfft4::destroy_group(p->grp);
     delete p;
 }
 
@@ -161,10 +166,13 @@ int sfft4_opts_default(sfft4_opts* o) {
     return SFFT4_OK;
 }
 
-int sfft4_plan(sfft4_plan_t* out, int64_t N, int64_t K, int32_t l, double q, uint64_t seed,
-               const sfft4_opts* opts) {
-    if (!out) return SFFT4_EINVAL;
-    *out = nullptr;
+}  // extern "C"
+
+namespace sfft4 {
+
+// Options with zero fields replaced by defaults, validated with the sizes (sfft4_plan's checks).
+int plan_options(int64_t N, int64_t K, int32_t l, double q, const sfft4_opts* opts, sfft4_opts* out,
+                 int* qn_out) {
     sfft4_opts o;
     sfft4_opts_default(&o);
     if (opts) {
@@ -184,29 +192,28 @@ int sfft4_plan(sfft4_plan_t* out, int64_t N, int64_t K, int32_t l, double q, uin
     if (o.precision != SFFT4_FP32 && o.precision != SFFT4_BF16X3) return SFFT4_EINVAL;
     if (o.max_batch < 1 || o.max_iters < 1 || o.max_iters > 256) return SFFT4_EINVAL;
     if (!(o.select_factor > 0) || !(o.mag_tol > 0) || o.min_votes < 0) return SFFT4_EINVAL;
+    if (o.l2_fetch_bytes > 128) return SFFT4_EINVAL;
     int64_t B1 = o.B1;
-    if (B1 == 0) B1 = std::max<int64_t>(kBMin, std::min<int64_t>({(int64_t)kBMax, N / 64, pow2ceil(2 * K)}));
-    if (B1 < kBMin || (B1 & (B1 - 1)) || B1 > N / 64 || B1 > kBMax) return SFFT4_EINVAL;
-
-    sfft4_plan_s* p = new (std::nothrow) sfft4_plan_s();
-    if (!p) return SFFT4_ENOMEM;
-    p->N = N;
-    p->n = ilog2(N);
-    p->K = K;
-    p->l = l;
-    p->qn = qn;
-    p->seed = seed;
-    p->o = o;
-    p->o.B1 = (int32_t)B1;
-    CK(cudaGetDevice(&p->device));
-    if (o.l2_fetch_bytes >= 0) {
-        // The gather reads one 8-byte sample per random 32-byte sector; a larger L2 fetch
-        // granularity would move 2-4x the needed DRAM bytes.  This is a limit of the
-        // calling process's CUDA context (a performance hint), not a device setting.
-        CK(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, o.l2_fetch_bytes ? o.l2_fetch_bytes : 32));
+    if (B1 == 0) {
+        B1 = std::max<int64_t>(kBMin, std::min<int64_t>({(int64_t)kBMax, N / 64, pow2ceil(2 * K)}));
+        // halve the default until the window of B1 buckets fits in N/2 (schedule of Section 3.1)
+        while (B1 > kBMin && 2 * window_halfwidth(B1, o.delta, nullptr) + 1 > N / 2) B1 >>= 1;
     }
+    if (B1 < kBMin || (B1 & (B1 - 1)) || B1 > N / 64 || B1 > kBMax) return SFFT4_EINVAL;
+    o.B1 = (int32_t)B1;
+    *out = o;
+    *qn_out = qn;
+    return SFFT4_OK;
+}
 
-    auto sch = schedule(K, B1, o.max_iters);
+// Host part of a plan: the static schedule of iterations (Section 3.1, reading R14), their
+// levels, offsets, thresholds and location tables (Section 3.2), fold segments, and the list
+// of bucket counts whose windows the plan needs.  No device work.
+int plan_schedule(sfft4_plan_s* p) {
+    const int64_t N = p->N, K = p->K;
+    const int l = p->l, qn = p->qn;
+    const sfft4_opts& o = p->o;
+    auto sch = schedule(K, o.B1, o.max_iters);
     p->Fcap = 0;
     for (size_t i = 0; i < sch.size(); ++i) {
         int64_t B = sch[i].first;
@@ -220,11 +227,11 @@ int sfft4_plan(sfft4_plan_t* out, int64_t N, int64_t K, int32_t l, double q, uin
         d.logL = ilog2(d.L);
         d.n_c = (int32_t)std::min<int64_t>(B, (int64_t)ceil(o.select_factor * std::max(sch[i].second, 1.0)));
         d.h = (int32_t)window_halfwidth(B, o.delta, nullptr);
-        if (2 * (int64_t)d.h + 1 > N / 2) { free_plan(p); return SFFT4_EINVAL; }
+        if (2 * (int64_t)d.h + 1 > N / 2) return SFFT4_EINVAL;
         // search region [bL - L, bL + L): pass band plus the transition bands (reading R5')
         std::vector<int64_t> lv = levels(2 * d.L, l, qn);
         int S = (int)lv.size();
-        if (S + 1 > kMaxRounds) { free_plan(p); return SFFT4_EINVAL; }
+        if (S + 1 > kMaxRounds) return SFFT4_EINVAL;
         d.S = S;
         d.R = S + 1;
         d.tau[0] = 0;
@@ -261,7 +268,7 @@ int sfft4_plan(sfft4_plan_t* out, int64_t N, int64_t K, int32_t l, double q, uin
         {
             int64_t rows = (2 * (int64_t)d.h + B) / B + 2;
             while (ih.Wj > 16 && (int64_t)kFoldRG * rows * ih.Wj * 4 > kFoldSmemMax) ih.Wj >>= 1;
-            if ((int64_t)kFoldRG * rows * ih.Wj * 4 > kFoldSmemMax) { free_plan(p); return SFFT4_EINVAL; }
+            if ((int64_t)kFoldRG * rows * ih.Wj * 4 > kFoldSmemMax) return SFFT4_EINVAL;
         }
         ih.unique = 0;
         for (int r0 = 0; r0 < d.R; r0 += kFoldRG) {
@@ -293,6 +300,7 @@ int sfft4_plan(sfft4_plan_t* out, int64_t N, int64_t K, int32_t l, double q, uin
             if (p->wins[k].B == B) wi = (int)k;
         if (wi < 0) {
             Window w;
+            w.N = N;
             w.B = (int32_t)B;
             w.h = d.h;
             w.L = d.L;
@@ -306,19 +314,34 @@ int sfft4_plan(sfft4_plan_t* out, int64_t N, int64_t K, int32_t l, double q, uin
         p->iters.push_back(ih);
     }
     p->Hlog = ilog2(2 * p->Fcap + 2);
+    return SFFT4_OK;
+}
 
-    CK(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device));
+// Device tables of a plan: window G, G'^ and FFT twiddles per bucket count (and the split DFT
+// matrices for BF16X3), then the iteration parameters.  With a cache, tables are shared by
+// (N, B) with other plans of a batch and owned by the cache.
+int plan_tables(sfft4_plan_s* p, std::vector<Window>* cache) {
+    int rc = check_cuda(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device));
+    if (rc) return rc;
     for (auto& w : p->wins) {
-        int rc = build_window_tables(p, &w, o.delta);
-        if (rc != SFFT4_OK) { free_plan(p); return rc; }
-        if (o.precision == SFFT4_BF16X3) {
-            CK(cudaMalloc(&w.dA1, dft_tc_matrix_bytes()));
-            CK(cudaMalloc(&w.dA2, dft_tc_matrix_bytes()));
-            CK(cudaMalloc(&w.tw4, (size_t)w.B * sizeof(float2)));
-            rc = build_dft_tc_tables(w.B, w.dA1, w.dA2, w.tw4);
-            if (rc != SFFT4_OK) { free_plan(p); return rc; }
+        if (cache) {
+            bool hit = false;
+            for (const Window& c : *cache)
+                if (c.N == w.N && c.B == w.B) { w = c; hit = true; break; }
+            if (hit) continue;
         }
+        rc = build_window_tables(p, &w, p->o.delta);
+        if (rc != SFFT4_OK) return rc;
+        if (p->o.precision == SFFT4_BF16X3) {
+            rc = check_cuda(cudaMalloc(&w.dA1, dft_tc_matrix_bytes()));
+            if (!rc) rc = check_cuda(cudaMalloc(&w.dA2, dft_tc_matrix_bytes()));
+            if (!rc) rc = check_cuda(cudaMalloc(&w.tw4, (size_t)w.B * sizeof(float2)));
+            if (!rc) rc = build_dft_tc_tables(w.B, w.dA1, w.dA2, w.tw4);
+            if (rc != SFFT4_OK) return rc;
+        }
+        if (cache) cache->push_back(w);
     }
+    if (cache) p->owns_tables = false;
     for (auto& ih : p->iters) {
         const Window& w = p->wins[ih.win];
         ih.d.G = w.G;
@@ -326,11 +349,45 @@ int sfft4_plan(sfft4_plan_t* out, int64_t N, int64_t K, int32_t l, double q, uin
         ih.d.tw = w.tw;
     }
     size_t ni = p->iters.size();
-    CK(cudaMalloc(&p->iters_dev, ni * sizeof(IterDev)));
+    rc = check_cuda(cudaMalloc(&p->iters_dev, ni * sizeof(IterDev)));
+    if (rc) return rc;
     std::vector<IterDev> hd(ni);
     for (size_t i = 0; i < ni; ++i) hd[i] = p->iters[i].d;
-    CK(cudaMemcpy(p->iters_dev, hd.data(), ni * sizeof(IterDev), cudaMemcpyHostToDevice));
+    return check_cuda(cudaMemcpy(p->iters_dev, hd.data(), ni * sizeof(IterDev), cudaMemcpyHostToDevice));
+}
 
+}  // namespace sfft4
+
+extern "C" {
+
+int sfft4_plan(sfft4_plan_t* out, int64_t N, int64_t K, int32_t l, double q, uint64_t seed,
+               const sfft4_opts* opts) {
+    if (!out) return SFFT4_EINVAL;
+    *out = nullptr;
+    sfft4_opts o;
+    int qn = 0;
+    int rc0 = plan_options(N, K, l, q, opts, &o, &qn);
+    if (rc0) return rc0;
+    sfft4_plan_s* p = new (std::nothrow) sfft4_plan_s();
+    if (!p) return SFFT4_ENOMEM;
+    p->N = N;
+    p->n = ilog2(N);
+    p->K = K;
+    p->l = l;
+    p->qn = qn;
+    p->seed = seed;
+    p->o = o;
+    CK(cudaGetDevice(&p->device));
+    if (o.l2_fetch_bytes >= 0) {
+        // The gather reads one 8-byte sample per random 32-byte sector; a larger L2 fetch
+        // granularity would move 2-4x the needed DRAM bytes.  This is a limit of the
+        // calling process's CUDA context (a performance hint), not a device setting.
+        CK(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, o.l2_fetch_bytes ? o.l2_fetch_bytes : 32));
+    }
+    int rc = plan_schedule(p);
+    if (!rc) rc = plan_tables(p, nullptr);
+    if (rc) { free_plan(p); return rc; }
+    const size_t ni = p->iters.size();
     size_t mb = (size_t)o.max_batch;
     size_t rb = (size_t)p->R_max * p->B_max;
     CK(cudaMalloc(&p->z, mb * rb * sizeof(float2)));
@@ -358,6 +415,37 @@ int sfft4_plan(sfft4_plan_t* out, int64_t N, int64_t K, int32_t l, double q, uin
     return SFFT4_OK;
 }
 
+int sfft4_plan_batched(sfft4_plan_t* out, int32_t nsig, const int64_t* N, const int64_t* K, int32_t l,
+                       double q, uint64_t seed, const sfft4_opts* opts) {
+    if (!out) return SFFT4_EINVAL;
+    *out = nullptr;
+    if (nsig < 1 || !N || !K) return SFFT4_EINVAL;
+    sfft4_opts o;
+    int qn = 0;
+    for (int32_t i = 0; i < nsig; ++i) {
+        int rc0 = plan_options(N[i], K[i], l, q, opts, &o, &qn);
+        if (rc0) return rc0;
+    }
+    sfft4_plan_s* p = new (std::nothrow) sfft4_plan_s();
+    if (!p) return SFFT4_ENOMEM;
+    p->l = l;
+    p->qn = qn;
+    p->seed = seed;
+    p->o = o;
+    p->o.trace = 0;
+    CK(cudaGetDevice(&p->device));
+    CK(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device));
+    if (o.l2_fetch_bytes >= 0)
+        CK(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, o.l2_fetch_bytes ? o.l2_fetch_bytes : 32));
+    CK(cudaMalloc(&p->status, sizeof(int32_t)));
+    CK(cudaMemset(p->status, 0, sizeof(int32_t)));
+    int rc = build_group_plan(p, nsig, N, K, l, q, seed, opts);
+    if (rc) { free_plan(p); return rc; }
+    CK(cudaDeviceSynchronize());
+    *out = p;
+    return SFFT4_OK;
+}
+
 void sfft4_destroy(sfft4_plan_t p) {
     if (!p) return;
     cudaDeviceSynchronize();
@@ -366,6 +454,7 @@ void sfft4_destroy(sfft4_plan_t p) {
 
 int sfft4_get_plan_info(sfft4_plan_t p, sfft4_plan_info* info) {
     if (!p || !info) return SFFT4_EINVAL;
+    if (p->grp) return SFFT4_ESTATE;
     memset(info, 0, sizeof(*info));
     info->N = p->N;
     info->K = p->K;
@@ -384,6 +473,7 @@ int sfft4_get_plan_info(sfft4_plan_t p, sfft4_plan_info* info) {
 }
 
 int sfft4_get_iter_info(sfft4_plan_t p, int32_t m, sfft4_iter_info* info) {
+    if (p && p->grp) return SFFT4_ESTATE;
     if (!p || !info || m < 1 || m > (int32_t)p->iters.size()) return SFFT4_EINVAL;
     const IterHost& ih = p->iters[m - 1];
     memset(info, 0, sizeof(*info));

@@ -50,6 +50,7 @@ struct IterDev {
 };
 
 struct Window {
+    int64_t N = 0;
     int32_t B, h;
     int64_t L;
     float* G = nullptr;        // device, 2h + 1
@@ -67,6 +68,53 @@ struct IterHost {
     int64_t unique;            // |union_s [tau_s - h, tau_s + h]|
     int32_t win;               // index into plan windows
     int32_t Wj;                // residues per fold CTA
+};
+
+// Arguments of one fold launch (uniform batch) or one fold job (batch of different sizes).
+struct FoldArgs {
+    const float2* x;
+    int64_t x_stride;
+    float2* z;
+    int64_t z_stride;
+    uint64_t N, seed;
+    int32_t m, signal0, B, logB, Wj, h, w, Mrows;
+    const float* G;
+    FoldGroup g;
+    int32_t tau[kFoldRG];
+    int32_t mlo[kFoldRG];   // first multiple m' of B with rows of round s in shared memory
+    int32_t soff[kFoldRG];  // (s Mrows - mlo_s) Wj: shared-memory offset of round s
+};
+
+struct FoldTile {
+    int32_t job, slice;
+};
+
+// Arguments of one decode launch (uniform batch) or one signal's decode (batch of sizes).
+struct DecodeArgs {
+    uint64_t N, seed;
+    int32_t n, signal0, first, l, qn, min_votes;
+    float mag_tol, sig_floor;
+    const IterDev* it;
+    float2* y;
+    int64_t y_stride;
+    int32_t* F;
+    int32_t* ff;
+    double2* fv;
+    int8_t* fvotes;
+    int64_t Fcap;
+    int32_t* hkeys;
+    int32_t* hvals;
+    int32_t Hlog;
+    float* theta;
+    int32_t* fxexp;
+};
+
+struct FinalJob {
+    const int32_t* F;
+    const int32_t* ff;
+    const double2* fv;
+    const int8_t* fvt;
+    int64_t Fcap, K;
 };
 
 // ------------------------------------------------------------------ device helpers ---
@@ -124,6 +172,8 @@ SFFT4_HD int64_t floor_div(int64_t a, int64_t b) {
     return q;
 }
 
+struct Group;  // batch of signals of different sizes (group.cu)
+
 }  // namespace sfft4
 
 // The opaque plan.
@@ -163,6 +213,12 @@ struct sfft4_plan_s {
     double2* trace_fv = nullptr;    // [iter][Fcap]
     int8_t* trace_votes = nullptr;  // [iter][Fcap]
     bool executed = false;
+    bool owns_tables = true;    // false when the window tables belong to a batch's cache
+    sfft4::Group* grp = nullptr;  // set for plans from sfft4_plan_batched
+    // CUDA graph of the last captured execute (opts.graph), keyed on its buffers
+    cudaStream_t gstream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    uint64_t gkey[8] = {};
     // profiling (opts.profile): event pairs recorded around launches, by kind
     struct Prof {
         cudaEvent_t a, b;
@@ -184,15 +240,41 @@ int launch_decode(sfft4_plan_s* p, int m_index, int nsig, cudaStream_t st);
 int launch_finalize(sfft4_plan_s* p, int nsig, int64_t* idx, sfft4_c128* val, int64_t* nfound,
                     int8_t* votes, cudaStream_t st);
 int launch_reset(sfft4_plan_s* p, int nsig, cudaStream_t st);
+FoldArgs make_fold_args(const sfft4_plan_s* p, int mi, const FoldGroup& g, size_t* smem_out);
+DecodeArgs make_decode_args(const sfft4_plan_s* p, int mi);
+size_t decode_smem_bytes(int B);
+int configure_kernels();
+int launch_fold_multi(int RG, const FoldArgs* jobs, const FoldTile* tiles, int ntiles,
+                      const float2* const* xptrs, int threads, size_t smem, cudaStream_t st);
+int launch_fft_multi(const float2* const* zcols, float2* const* ycols, int ncols, int B,
+                     const float2* tw, cudaStream_t st);
+int launch_decode_multi(int rclass, const DecodeArgs* jobs, const int32_t* list, int n, size_t smem,
+                        cudaStream_t st);
+int launch_finalize_multi(const FinalJob* jobs, int nsig, int64_t Kout, int64_t* idx, sfft4_c128* val,
+                          int64_t* nfound, int8_t* votes, cudaStream_t st);
 int prof_begin(sfft4_plan_s* p, cudaStream_t st, cudaEvent_t* a);
 int prof_end(sfft4_plan_s* p, cudaStream_t st, cudaEvent_t a, int kind, int64_t samples);
 enum { kProfFold = 0, kProfFft = 1, kProfDecode = 2, kProfFinalize = 3 };
 int check_cuda(cudaError_t e);
+// Runs body(stream) directly, or (opts.graph) replays the graph captured from it for the
+// same key, capturing it first on the plan's private stream.
+int graph_run(sfft4_plan_s* p, const uint64_t key[8], cudaStream_t st, int (*body)(sfft4_plan_s*, const void*, cudaStream_t),
+              const void* ctx);
+// Implemented in group.cu.
+int build_group_plan(sfft4_plan_s* p, int nsig, const int64_t* N, const int64_t* K, int32_t l, double q,
+                     uint64_t seed, const sfft4_opts* opts);
+void destroy_group(Group* g);
+// Implemented in plan.cu.
+int plan_options(int64_t N, int64_t K, int32_t l, double q, const sfft4_opts* opts, sfft4_opts* out,
+                 int* qn_out);
+int plan_schedule(sfft4_plan_s* p);
+int plan_tables(sfft4_plan_s* p, std::vector<Window>* cache);
 // Implemented in dft_tc.cu.
 size_t dft_tc_matrix_bytes();
 int build_dft_tc_tables(int B, unsigned char* A1, unsigned char* A2, float2* tw4);
 int configure_dft_tc();
 int launch_dft_tc(const float2* z, int64_t z_stride, float2* u, float2* y, int64_t y_stride, int nsig,
                   int R, int B, const unsigned char* A1, const unsigned char* A2, const float2* tw4,
-                  int32_t* status, int sm_count, cudaStream_t st);
+                  int32_t* status, int sm_count, cudaStream_t st, const float2* const* zcols = nullptr,
+                  float2* const* ucols = nullptr, float2* const* ycols = nullptr, int64_t ncols_override = 0);
 }  // namespace sfft4

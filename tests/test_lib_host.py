@@ -28,7 +28,8 @@ def declared_functions():
 def test_header_declares_expected_entry_points():
     names = declared_functions()
     for need in ("sfft4_plan", "sfft4_execute", "sfft4_execute_batched", "sfft4_destroy",
-                 "sfft4_strerror", "sfft4_get_plan_info", "sfft4_bucketize"):
+                 "sfft4_strerror", "sfft4_get_plan_info", "sfft4_bucketize", "sfft4_plan_batched",
+                 "sfft4_execute_batched_v", "sfft4_get_batch_info"):
         assert need in names
 
 
@@ -47,14 +48,17 @@ def test_struct_layouts_match_c(tmp_path):
     from paper_2011_05698_gb300 import _lib
     src = tmp_path / "sz.c"
     src.write_text('#include "sfft4.h"\n#include <stdio.h>\n#include <stddef.h>\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(sfft4_opts), '
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(sfft4_opts), '
                    'sizeof(sfft4_plan_info), sizeof(sfft4_iter_info), offsetof(sfft4_iter_info, tau), '
-                   'offsetof(sfft4_iter_info, unique_samples), sizeof(sfft4_c128)); return 0;}\n')
+                   'offsetof(sfft4_iter_info, unique_samples), sizeof(sfft4_c128), '
+                   'offsetof(sfft4_opts, graph), sizeof(sfft4_batch_info), '
+                   'offsetof(sfft4_batch_info, samples_per_execute)); return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     want = [ctypes.sizeof(_lib.Opts), ctypes.sizeof(_lib.PlanInfo), ctypes.sizeof(_lib.IterInfo),
-            _lib.IterInfo.tau.offset, _lib.IterInfo.unique_samples.offset, ctypes.sizeof(_lib.C128)]
+            _lib.IterInfo.tau.offset, _lib.IterInfo.unique_samples.offset, ctypes.sizeof(_lib.C128),
+            _lib.Opts.graph.offset, ctypes.sizeof(_lib.BatchInfo), _lib.BatchInfo.samples_per_execute.offset]
     assert got == want
 
 
@@ -109,7 +113,27 @@ def test_execute_rejects_null_arguments(lib):
     assert lib.sfft4_execute_batched(None, 1, None, 0, None, None, None, None, None) == _lib.SFFT4_EINVAL
     assert lib.sfft4_get_plan_info(None, None) == _lib.SFFT4_EINVAL
     assert lib.sfft4_trace_get(None, 1, None, 0, None, None, None, None) == _lib.SFFT4_EINVAL
+    assert lib.sfft4_execute_batched_v(None, None, None, None, None, None, None) == _lib.SFFT4_EINVAL
+    assert lib.sfft4_get_batch_info(None, None) == _lib.SFFT4_EINVAL
     lib.sfft4_destroy(None)
+
+
+def test_plan_batched_rejects_invalid_sizes(lib):
+    from paper_2011_05698_gb300 import _lib
+    h = ctypes.c_void_p()
+
+    def arr(v):
+        return (ctypes.c_int64 * len(v))(*v)
+
+    # one bad signal anywhere in the batch rejects the whole plan, before any device work
+    for Ns, Ks in [([2**14, 1000], [16, 4]), ([2**14, 2**16], [16, 0]), ([2**14], [300])]:
+        assert lib.sfft4_plan_batched(ctypes.byref(h), len(Ns), arr(Ns), arr(Ks), 16, 1.0, 0, None) \
+            == _lib.SFFT4_EINVAL
+        assert not h.value
+    assert lib.sfft4_plan_batched(ctypes.byref(h), 0, arr([2**14]), arr([16]), 16, 1.0, 0, None) \
+        == _lib.SFFT4_EINVAL
+    assert lib.sfft4_plan_batched(ctypes.byref(h), 1, None, None, 16, 1.0, 0, None) == _lib.SFFT4_EINVAL
+    assert lib.sfft4_plan_batched(None, 1, arr([2**14]), arr([16]), 16, 1.0, 0, None) == _lib.SFFT4_EINVAL
 
 
 def test_binding_fails_loudly_without_cuda():
