@@ -180,6 +180,51 @@ def device_batch(N, K, S, seed0, snr, device):
     return xs
 
 
+def uneven_form(s4, args, dev, stream, dist):
+    """The uneven batch: 512 signals, N log-uniform over 2^16..2^22, K log-uniform in
+    [10, 2000] capped at N/64, SNR uniform in [10, 40] dB; one BatchPlan execute per step,
+    replayed as a CUDA graph, BF16x3 DFT.  Kernel times come from a second, profiled plan."""
+    import torch
+    from synth.signals import device_signal, signal_seed, uneven_sizes
+    nsig, seed = args.uneven_signals, 2026
+    Ns, Ks, snrs = uneven_sizes(nsig, seed)
+    xs = [device_signal(int(Ns[i]), int(Ks[i]), signal_seed(seed, i), snrs[i], dev)[0] for i in range(nsig)]
+    graph = not args.no_graph
+    bp = s4.BatchPlan(Ns.tolist(), Ks.tolist(), L_DEF, Q_DEF, seed=seed, precision=args.precision, graph=graph)
+    out = bp.outputs()
+    ptrs = bp.pointers(xs)
+
+    def step():
+        bp.execute(xs, out=out, ptrs=ptrs)
+
+    steps = max(3, min(args.steps, 20))
+    el = timed(step, steps, args.warmup, stream, dist)
+    if dist is not None:
+        t = torch.tensor([el], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    world = dist.get_world_size() if dist is not None else 1
+    info = dict(bp.info)
+    bp.close()
+    bq = s4.BatchPlan(Ns.tolist(), Ks.tolist(), L_DEF, Q_DEF, seed=seed, precision=args.precision, profile=True)
+    outq = bq.outputs()
+    bq.execute(xs, out=outq)
+    torch.cuda.synchronize()
+    bq.profile(reset=True)
+    bq.execute(xs, out=outq)
+    prof = bq.profile(reset=True)
+    bq.close()
+    fold_gbs = 8.0 * prof["fold_samples"] / (prof["fold_ms"] / 1e3) / 1e9 if prof["fold_ms"] > 0 else None
+    return {"value": nsig * steps * world / el, "unit": "transforms/s", "ms_per_step": 1e3 * el / steps,
+            "steps": steps, "signals": nsig, "precision": args.precision, "graph": graph,
+            "samples_per_step": info["samples_per_execute"], "kernels_per_step": info["kernels_per_execute"],
+            "graph_launches_per_step": 1 if graph else 0, "levels": info["n_levels"], "classes": info["n_classes"],
+            "workload": "512 signals: N=2^n, n uniform on 16..22; K=round(exp U[ln 10, ln 2000]) <= N/64; "
+                        "SNR U[10, 40] dB; l=16, q=1",
+            "fold_gbs_useful": fold_gbs,
+            "kernel_ms_one_execute": {k: prof[k + "_ms"] for k in ("fold", "fft", "decode", "finalize")}}
+
+
 def timed(fn, steps, warmup, stream, dist=None):
     import torch
     for _ in range(warmup):
@@ -208,10 +253,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--snr", type=float, default=SNR_DEF)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"])
+    ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16x3"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--plain-signals", type=int, default=16)
+    ap.add_argument("--uneven-signals", type=int, default=512)
+    ap.add_argument("--no-fp32-form", action="store_true")
+    ap.add_argument("--form", default="all", choices=["all", "uneven"],
+                    help="uneven: time only the uneven-batch form and print its line")
+    ap.add_argument("--no-graph", action="store_true", help="uneven form without CUDA-graph replay")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -225,7 +275,7 @@ def main():
     # the oracle pool starts (spawn) before the first CUDA call
     pool = None
     cpu_workers = max(1, min(host_cores(), 8))
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and not args.no_cpu and args.form == "all":
         pool = make_pool(cpu_workers)
 
     import torch
@@ -239,6 +289,14 @@ def main():
     from paper_2011_05698_gb300 import build
     build.build()
     import paper_2011_05698_gb300 as s4
+
+    if args.form == "uneven":
+        u = uneven_form(s4, args, dev, torch.cuda.current_stream(dev), dist)
+        if rank == 0:
+            print(json.dumps({"form": "uneven_batch", **u}), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
 
     S = args.batch
     plan = s4.Plan(N_DEF, K_DEF, L_DEF, Q_DEF, seed=1234, max_batch=S, profile=True,
@@ -318,6 +376,37 @@ def main():
                "d2h_bytes_per_step": d2h, "batch": Se}
         plan_e.close()
 
+    # the same batch with the FP32 radix-2 DFT
+    fp32_form = None
+    if not args.no_fp32_form and args.precision != "fp32":
+        plan_f = s4.Plan(N_DEF, K_DEF, L_DEF, Q_DEF, seed=1234, max_batch=S, precision="fp32")
+        outf = plan_f._outputs(S)
+        steps_f = max(3, min(args.steps, 50))
+        ef = timed(lambda: plan_f.execute_batched(xs, outf), steps_f, args.warmup, stream, dist)
+        fp32_form = {"value": S * steps_f * world / ef, "unit": "transforms/s", "steps": steps_f,
+                     "form": "batched sfft4_execute_batched, FP32 radix-2 DFT"}
+        plan_f.close()
+
+    # crossover context: a dense length-N FFT (cuFFT through torch, outside the library) of
+    # the same signals, 32 per call
+    dense = None
+    chunk = min(S, 32)
+    yd = torch.empty((chunk, N_DEF), dtype=torch.complex64, device=dev)
+
+    def step_d():
+        for c0 in range(0, S, chunk):
+            torch.fft.fft(xs[c0:c0 + chunk], out=yd)
+
+    steps_d = max(3, min(args.steps, 20))
+    ed = timed(step_d, steps_d, args.warmup, stream, None)
+    dense = {"value": S * steps_d / ed, "unit": "transforms/s", "form": "torch.fft.fft (cuFFT) of the same "
+             "complex64 signals, full N-point spectrum, not part of the library"}
+    del yd
+
+    uneven = None
+    if args.uneven_signals > 0:
+        uneven = uneven_form(s4, args, dev, stream, dist)
+
     # plain form: one signal per execute call, FP32 DFT
     plain = None
     if args.plain_signals > 0:
@@ -356,7 +445,8 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": plan.info["kernels_per_execute"] * args.steps,
                 "clocks": clk.summary(), "forms": {"batched": {"value": value, "precision": args.precision},
-                                                   "plain_fp32": plain}}
+                                                   "batched_fp32": fp32_form, "plain_fp32": plain,
+                                                   "uneven_batch": uneven, "dense_fft_context": dense}}
         print(json.dumps(line), flush=True)
     plan.close()
     if dist is not None:
