@@ -15,6 +15,9 @@
 #include <stdio.h>
 
 #include <cuda_bf16.h>
+#include <string.h>
+
+#include <vector>
 
 #include "sfft4_internal.cuh"
 
@@ -92,18 +95,28 @@ __global__ void k_dft_twiddles(float2* tw4, int B, int B1, int B2) {
     (void)B2;
 }
 
-struct DftArgs {
+// One (DFT matrix, stage) group of a launch: nvec input vectors of length P, 64 / P per GEMM
+// column; columns come from per-column pointer tables or from (signal, round) strides.
+struct DftGroup {
     const float2* in;
-    int64_t in_stride;     // per signal
+    int64_t in_stride;             // per signal (strided form)
     float2* out;
-    int64_t out_stride;    // per signal
-    const unsigned char* A;  // three bf16 pieces in core-matrix layout
-    const float2* tw4;     // stage 2 twiddles (B entries)
-    int32_t* status;       // set to 1 if a bounded wait gave up
-    const float2* const* in_cols;  // optional per-column input base pointers (else strides)
+    int64_t out_stride;
+    const float2* const* in_cols;  // optional per-column input base pointers
     float2* const* out_cols;       // optional per-column output base pointers
-    int B, B1, B2, R, P, copies, stage;  // stage 0: single (P = B); 1: four-step first; 2: second
-    int64_t nvec, ngcols;
+    const unsigned char* A;        // three bf16 pieces in core-matrix layout
+    const float2* tw4;             // stage 2 twiddles (B entries)
+    int B, B1, B2, R, P, copies, stage, pad;  // stage 0: single (P = B); 1, 2: four-step
+    int64_t nvec, ngcols, tile0;   // tile0: first tile of this group in the launch's list
+};
+
+constexpr int kDftMaxGroups = 12;
+
+struct DftLaunch {
+    DftGroup g[kDftMaxGroups];
+    int32_t ngroups;
+    int32_t* status;               // set to 1 if a bounded wait gave up
+    int64_t ntiles;
 };
 
 __device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
@@ -114,7 +127,103 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16&
     c = __float2bfloat16_rn(r2);
 }
 
-__global__ void __launch_bounds__(kDftThreads, 1) k_dft_bf16x3(const DftArgs a) {
+// Tile range [lo, hi) of the launch's tile list owned by CTA b of G (contiguous, so a CTA
+// changes DFT matrix at most a few times).
+__device__ __forceinline__ void cta_tiles(int64_t T, int64_t* lo, int64_t* hi) {
+    *lo = (int64_t)blockIdx.x * T / gridDim.x;
+    *hi = (int64_t)(blockIdx.x + 1) * T / gridDim.x;
+}
+
+__device__ __forceinline__ int group_of(const DftLaunch& L, int64_t ti) {
+    int gi = 0;
+    while (gi + 1 < L.ngroups && ti >= L.g[gi + 1].tile0) ++gi;
+    return gi;
+}
+
+// Gather the two work items of this thread for tile ti of group g into registers.  A work
+// item is 8 consecutive elements of one input vector; GEMM column n of the tile holds vectors
+// v = (g0 + n) copies + cc, K rows cc 2P + e (re) and cc 2P + P + e (im) hold element e.
+__device__ __forceinline__ void dft_gather(const DftGroup& g, int64_t ti, int tid, float2 (&val)[2][8]) {
+    const int P = g.P, copies = g.copies, B = g.B, B1 = g.B1, B2 = g.B2, R = g.R;
+    const int64_t g0 = (ti - g.tile0) * kNT;
+    const int chunks = P >> 3;
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+        const int item = tid + w * kDftThreads;
+        const int n = item % kNT, rest = item / kNT;
+        const int cc = rest / chunks, e0 = (rest - cc * chunks) * 8;
+        const int64_t v = (g0 + n) * copies + cc;
+        if (g0 + n < g.ngcols && v < g.nvec) {
+            if (g.stage == 0) {
+                const float2* cb = g.in_cols ? g.in_cols[v] : g.in + (v / R) * g.in_stride + (v % R) * B;
+                const float4* src = (const float4*)(cb + e0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 f = __ldg(src + q);
+                    val[w][2 * q] = make_float2(f.x, f.y);
+                    val[w][2 * q + 1] = make_float2(f.z, f.w);
+                }
+            } else if (g.stage == 1) {
+                const int64_t col = v / B2;
+                const int j2 = (int)(v - col * B2);
+                const float2* cb = g.in_cols ? g.in_cols[col] : g.in + (col / R) * g.in_stride + (col % R) * B;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) val[w][q] = __ldg(cb + j2 + (int64_t)B2 * (e0 + q));
+            } else {
+                // stage 2 reads the stage-1 output written by the previous launch: plain loads
+                const int64_t col = v / B1;
+                const int k1 = (int)(v - col * B1);
+                const float2* cb = g.in_cols ? g.in_cols[col] : g.in + (col / R) * g.in_stride + (col % R) * B;
+                const float4* src = (const float4*)(cb + (int64_t)k1 * B2 + e0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 f = src[q];
+                    val[w][2 * q] = make_float2(f.x, f.y);
+                    val[w][2 * q + 1] = make_float2(f.z, f.w);
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float2 tw = __ldg(g.tw4 + (e0 + q) * B1 + k1);
+                    const float2 u = val[w][q];
+                    val[w][q] = make_float2(u.x * tw.x - u.y * tw.y, u.x * tw.y + u.y * tw.x);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) val[w][q] = make_float2(0.f, 0.f);
+        }
+    }
+}
+
+// Split the gathered items into the three bf16 X pieces (core-matrix layout).
+__device__ __forceinline__ void dft_store_x(const DftGroup& g, int tid, const float2 (&val)[2][8],
+                                            unsigned char* sX) {
+    const int P = g.P, chunks = P >> 3;
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+        const int item = tid + w * kDftThreads;
+        const int n = item % kNT, rest = item / kNT;
+        const int cc = rest / chunks, e0 = (rest - cc * chunks) * 8;
+        __align__(16) __nv_bfloat16 re[3][8], imv[3][8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            split3(val[w][q].x, re[0][q], re[1][q], re[2][q]);
+            split3(val[w][q].y, imv[0][q], imv[1][q], imv[2][q]);
+        }
+        const int ore = core_off(n, cc * 2 * P + e0), oim = core_off(n, cc * 2 * P + P + e0);
+#pragma unroll
+        for (int pc = 0; pc < 3; ++pc) {
+            *(uint4*)(sX + pc * kPieceBytes + ore) = *(const uint4*)re[pc];
+            *(uint4*)(sX + pc * kPieceBytes + oim) = *(const uint4*)imv[pc];
+        }
+    }
+}
+
+// Persistent CTAs over the tile list of up to kDftMaxGroups (matrix, stage) groups.  Per tile:
+// the gathered registers are split into X, one thread issues the 8 K-steps x 6 products, the
+// next tile's gather is issued while the MMAs run, then the accumulator goes through TMEM ->
+// shared stage -> coalesced stores.
+__global__ void __launch_bounds__(kDftThreads, 1) k_dft_bf16x3(const __grid_constant__ DftLaunch L) {
     static_assert(kDftThreads == 512 && kNT == 128, "epilogue maps 4 warpgroups to 4 x 32 columns");
     extern __shared__ unsigned char smraw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
@@ -123,10 +232,10 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_dft_bf16x3(const DftArgs a) 
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5;
+    int64_t t_lo, t_hi;
+    cta_tiles(L.ntiles, &t_lo, &t_hi);
+    if (t_lo >= t_hi) return;
 
-    // A: straight copy of the pre-laid-out pieces (16-byte vectors)
-    for (int i = tid; i < 3 * kPieceBytes / 16; i += kDftThreads)
-        ((uint4*)sA)[i] = __ldg((const uint4*)a.A + i);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
                      "r"(kNT));
@@ -141,75 +250,20 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_dft_bf16x3(const DftArgs a) 
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
 
-    const int P = a.P, copies = a.copies, B = a.B, B1 = a.B1, B2 = a.B2, R = a.R;
-    const int64_t ntiles = (a.ngcols + kNT - 1) / kNT;
     uint32_t phase = 0;
-    bool ok = true;
-    for (int64_t ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
-        const int64_t g0 = ti * kNT;
-        // ---- gather the tile's input vectors into the three X pieces -----------------
-        // GEMM column n holds vectors v = (g0 + n) copies + cc; K rows cc 2P + e (re) and
-        // cc 2P + P + e (im) hold element e of vector cc.  One work item = 8 consecutive
-        // elements of one vector (P >= 8): two 16-byte core rows (re and im) per piece.
-        {
-            const int chunks = P >> 3;
-            for (int item = tid; item < kNT * 8; item += kDftThreads) {
-                const int n = item % kNT, rest = item / kNT;
-                const int cc = rest / chunks, e0 = (rest - cc * chunks) * 8;
-                const int64_t v = (g0 + n) * copies + cc;
-                float2 val[8];
-                if (g0 + n < a.ngcols && v < a.nvec) {
-                    if (a.stage == 0) {
-                        const float2* cb = a.in_cols ? a.in_cols[v] : a.in + (v / R) * a.in_stride + (v % R) * B;
-                        const float4* src = (const float4*)(cb + e0);
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const float4 f = src[q];
-                            val[2 * q] = make_float2(f.x, f.y);
-                            val[2 * q + 1] = make_float2(f.z, f.w);
-                        }
-                    } else if (a.stage == 1) {
-                        const int64_t col = v / B2;
-                        const int j2 = (int)(v - col * B2);
-                        const float2* cb = a.in_cols ? a.in_cols[col] : a.in + (col / R) * a.in_stride + (col % R) * B;
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) val[q] = cb[j2 + (int64_t)B2 * (e0 + q)];
-                    } else {
-                        const int64_t col = v / B1;
-                        const int k1 = (int)(v - col * B1);
-                        const float2* cb = a.in_cols ? a.in_cols[col] : a.in + (col / R) * a.in_stride + (col % R) * B;
-                        const float4* src = (const float4*)(cb + (int64_t)k1 * B2 + e0);
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const float4 f = src[q];
-                            val[2 * q] = make_float2(f.x, f.y);
-                            val[2 * q + 1] = make_float2(f.z, f.w);
-                        }
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const float2 w = a.tw4[(e0 + q) * B1 + k1];
-                            const float2 u = val[q];
-                            val[q] = make_float2(u.x * w.x - u.y * w.y, u.x * w.y + u.y * w.x);
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) val[q] = make_float2(0.f, 0.f);
-                }
-                __align__(16) __nv_bfloat16 re[3][8], imv[3][8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    split3(val[q].x, re[0][q], re[1][q], re[2][q]);
-                    split3(val[q].y, imv[0][q], imv[1][q], imv[2][q]);
-                }
-                const int ore = core_off(n, cc * 2 * P + e0), oim = core_off(n, cc * 2 * P + P + e0);
-#pragma unroll
-                for (int pc = 0; pc < 3; ++pc) {
-                    *(uint4*)(sX + pc * kPieceBytes + ore) = *(const uint4*)re[pc];
-                    *(uint4*)(sX + pc * kPieceBytes + oim) = *(const uint4*)imv[pc];
-                }
-            }
+    int cur = -1;  // group whose matrix is in sA
+    float2 val[2][8];
+    int gi = group_of(L, t_lo);
+    dft_gather(L.g[gi], t_lo, tid, val);
+    for (int64_t ti = t_lo; ti < t_hi; ++ti) {
+        const DftGroup& g = L.g[gi];
+        if (gi != cur) {
+            // the previous tile's MMAs have completed, so A may be replaced
+            for (int i = tid; i < 3 * kPieceBytes / 16; i += kDftThreads)
+                ((uint4*)sA)[i] = __ldg((const uint4*)g.A + i);
+            cur = gi;
         }
+        dft_store_x(g, tid, val, sX);
         asm volatile("fence.proxy.async.shared::cta;");
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
@@ -232,6 +286,9 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_dft_bf16x3(const DftArgs a) 
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 smem_u32(&mbar)));
         }
+        // ---- the next tile's gather is in flight while the MMAs run ---------------------
+        const int gn = (ti + 1 < t_hi) ? group_of(L, ti + 1) : gi;
+        if (ti + 1 < t_hi) dft_gather(L.g[gn], ti + 1, tid, val);
         // ---- bounded wait for the accumulator -------------------------------------------
         uint32_t done = 0;
         for (uint32_t it = 0; it < kWaitLimit && !done; ++it) {
@@ -243,8 +300,7 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_dft_bf16x3(const DftArgs a) 
         }
         phase ^= 1u;
         if (!__syncthreads_and(done)) {
-            if (tid == 0) atomicExch(a.status, 1);
-            ok = false;
+            if (tid == 0) atomicExch(L.status, 1);
             break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
@@ -267,46 +323,51 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_dft_bf16x3(const DftArgs a) 
                 for (int j = 0; j < 16; ++j) stg[row * (kNT + 1) + c0 + j] = __uint_as_float(d[j]);
             }
         }
-        __syncthreads();
-        // output items (n, cc, k): stage 0 keeps k fastest (contiguous outputs), stages 1-2
-        // keep n fastest (consecutive GEMM columns are consecutive output positions)
-        for (int item = tid; item < kNT * 64; item += kDftThreads) {
-            int n, cc, k;
-            if (a.stage == 0) {
-                k = item % P;
-                const int rest = item / P;
-                cc = rest % copies;
-                n = rest / copies;
-            } else {
-                n = item % kNT;
-                const int rest = item / kNT;
-                cc = rest / P;
-                k = rest - cc * P;
-            }
-            const int64_t g = g0 + n;
-            const int64_t v = g * copies + cc;
-            if (g >= a.ngcols || v >= a.nvec) continue;
-            const float2 val = make_float2(stg[(cc * 2 * P + k) * (kNT + 1) + n],
-                                           stg[(cc * 2 * P + P + k) * (kNT + 1) + n]);
-            int64_t col, off;
-            if (a.stage == 0) {
-                col = v;
-                off = k;
-            } else if (a.stage == 1) {
-                col = v / B2;
-                const int j2 = (int)(v - col * B2);
-                off = (int64_t)k * B2 + j2;
-            } else {
-                col = v / B1;
-                const int k1 = (int)(v - col * B1);
-                off = k1 + (int64_t)B1 * k;
-            }
-            float2* ob = a.out_cols ? a.out_cols[col] : a.out + (col / R) * a.out_stride + (col % R) * B;
-            ob[off] = val;
-        }
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
+        {
+            const int P = g.P, copies = g.copies, B1 = g.B1, B2 = g.B2, R = g.R, B = g.B;
+            const int64_t g0 = (ti - g.tile0) * kNT;
+            // output items (n, cc, k): stage 0 keeps k fastest (contiguous outputs), stages 1-2
+            // keep n fastest (consecutive GEMM columns are consecutive output positions)
+            for (int item = tid; item < kNT * 64; item += kDftThreads) {
+                int n, cc, k;
+                if (g.stage == 0) {
+                    k = item % P;
+                    const int rest = item / P;
+                    cc = rest % copies;
+                    n = rest / copies;
+                } else {
+                    n = item % kNT;
+                    const int rest = item / kNT;
+                    cc = rest / P;
+                    k = rest - cc * P;
+                }
+                const int64_t gc = g0 + n;
+                const int64_t v = gc * copies + cc;
+                if (gc >= g.ngcols || v >= g.nvec) continue;
+                const float2 o = make_float2(stg[(cc * 2 * P + k) * (kNT + 1) + n],
+                                             stg[(cc * 2 * P + P + k) * (kNT + 1) + n]);
+                int64_t col, off;
+                if (g.stage == 0) {
+                    col = v;
+                    off = k;
+                } else if (g.stage == 1) {
+                    col = v / B2;
+                    const int j2 = (int)(v - col * B2);
+                    off = (int64_t)k * B2 + j2;
+                } else {
+                    col = v / B1;
+                    const int k1 = (int)(v - col * B1);
+                    off = k1 + (int64_t)B1 * k;
+                }
+                float2* ob = g.out_cols ? g.out_cols[col] : g.out + (col / R) * g.out_stride + (col % R) * B;
+                ob[off] = o;
+            }
+        }
+        __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
+        gi = gn;
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -340,45 +401,114 @@ int configure_dft_tc() {
     return check_cuda(cudaFuncSetAttribute(k_dft_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize, kDftSmem));
 }
 
+namespace {
+
+DftGroup make_group(int stage, int B, int P, const unsigned char* A, const float2* tw4, int64_t nvec) {
+    DftGroup g;
+    memset(&g, 0, sizeof(g));
+    int B1, B2;
+    dft_factor(B, &B1, &B2);
+    g.B = B;
+    g.B1 = B1;
+    g.B2 = B2;
+    g.R = 1;
+    g.P = P;
+    g.copies = 64 / P;
+    g.stage = stage;
+    g.A = A;
+    g.tw4 = tw4;
+    g.nvec = nvec;
+    g.ngcols = (nvec + g.copies - 1) / g.copies;
+    return g;
+}
+
+// One launch over up to kDftMaxGroups groups (tiles numbered group after group).
+int launch_groups(std::vector<DftGroup>& gs, int32_t* status, int sm_count, cudaStream_t st) {
+    size_t i0 = 0;
+    while (i0 < gs.size()) {
+        DftLaunch L;
+        memset(&L, 0, sizeof(L));
+        L.status = status;
+        int64_t T = 0;
+        int n = 0;
+        for (; n < kDftMaxGroups && i0 + n < gs.size(); ++n) {
+            DftGroup g = gs[i0 + n];
+            g.tile0 = T;
+            T += (g.ngcols + kNT - 1) / kNT;
+            L.g[n] = g;
+        }
+        L.ngroups = n;
+        L.ntiles = T;
+        i0 += n;
+        if (T == 0) continue;
+        const int grid = (int)(T < sm_count ? T : sm_count);
+        k_dft_bf16x3<<<grid, kDftThreads, kDftSmem, st>>>(L);
+        int rc = check_cuda(cudaGetLastError());
+        if (rc) return rc;
+    }
+    return SFFT4_OK;
+}
+
+}  // namespace
+
 // B-point DFTs of nsig x R columns of z (stride z_stride per signal) into y (stride
 // y_stride), through the scratch u (same layout as z) for the four-step case.
 int launch_dft_tc(const float2* z, int64_t z_stride, float2* u, float2* y, int64_t y_stride, int nsig,
                   int R, int B, const unsigned char* A1, const unsigned char* A2, const float2* tw4,
-                  int32_t* status, int sm_count, cudaStream_t st, const float2* const* zcols,
-                  float2* const* ucols, float2* const* ycols, int64_t ncols_override) {
+                  int32_t* status, int sm_count, cudaStream_t st) {
     int B1, B2;
     dft_factor(B, &B1, &B2);
-    DftArgs a;
-    a.tw4 = tw4;
-    a.status = status;
-    a.B = B;
-    a.B1 = B1;
-    a.B2 = B2;
-    a.R = R;
-    const int64_t ncols = ncols_override > 0 ? ncols_override : (int64_t)nsig * R;
-    auto run = [&](int stage, const float2* in, int64_t is, float2* out, int64_t os, int P,
-                   const unsigned char* A, int64_t nvec, const float2* const* icols, float2* const* ocols) {
-        a.stage = stage;
-        a.in_cols = icols;
-        a.out_cols = ocols;
-        a.in = in;
-        a.in_stride = is;
-        a.out = out;
-        a.out_stride = os;
-        a.P = P;
-        a.copies = 64 / P;
-        a.A = A;
-        a.nvec = nvec;
-        a.ngcols = (nvec + a.copies - 1) / a.copies;
-        const int64_t ntiles = (a.ngcols + kNT - 1) / kNT;
-        const int grid = (int)(ntiles < sm_count ? ntiles : sm_count);
-        k_dft_bf16x3<<<grid, kDftThreads, kDftSmem, st>>>(a);
-        return check_cuda(cudaGetLastError());
-    };
-    if (B2 == 1) return run(0, z, z_stride, y, y_stride, B, A1, ncols, zcols, ycols);
-    int rc = run(1, z, z_stride, u, z_stride, B1, A1, ncols * B2, zcols, ucols);
+    const int64_t ncols = (int64_t)nsig * R;
+    std::vector<DftGroup> gs(1);
+    if (B2 == 1) {
+        gs[0] = make_group(0, B, B, A1, tw4, ncols);
+        gs[0].in = z, gs[0].in_stride = z_stride, gs[0].out = y, gs[0].out_stride = y_stride, gs[0].R = R;
+        return launch_groups(gs, status, sm_count, st);
+    }
+    gs[0] = make_group(1, B, B1, A1, tw4, ncols * B2);
+    gs[0].in = z, gs[0].in_stride = z_stride, gs[0].out = u, gs[0].out_stride = z_stride, gs[0].R = R;
+    int rc = launch_groups(gs, status, sm_count, st);
     if (rc) return rc;
-    return run(2, u, z_stride, y, y_stride, B2, A2, ncols * B1, (const float2* const*)ucols, ycols);
+    gs[0] = make_group(2, B, B2, A2, tw4, ncols * B1);
+    gs[0].in = u, gs[0].in_stride = z_stride, gs[0].out = y, gs[0].out_stride = y_stride, gs[0].R = R;
+    return launch_groups(gs, status, sm_count, st);
+}
+
+// DFTs of column sets of several bucket counts (a level of a batch of uneven signals): one
+// launch for the single-stage and first four-step stages of every set, one for the second.
+int launch_dft_tc_sets(const DftColSet* sets, int nsets, int32_t* status, int sm_count, cudaStream_t st) {
+    std::vector<DftGroup> a, b;
+    for (int i = 0; i < nsets; ++i) {
+        const DftColSet& c = sets[i];
+        int B1, B2;
+        dft_factor(c.B, &B1, &B2);
+        if (B2 == 1) {
+            DftGroup g = make_group(0, c.B, c.B, c.A1, c.tw4, c.ncols);
+            g.in_cols = c.zcols, g.out_cols = c.ycols;
+            a.push_back(g);
+        } else {
+            DftGroup g1 = make_group(1, c.B, B1, c.A1, c.tw4, c.ncols * B2);
+            g1.in_cols = c.zcols, g1.out_cols = c.ucols;
+            a.push_back(g1);
+            DftGroup g2 = make_group(2, c.B, B2, c.A2, c.tw4, c.ncols * B1);
+            g2.in_cols = (const float2* const*)c.ucols, g2.out_cols = c.ycols;
+            b.push_back(g2);
+        }
+    }
+    int rc = launch_groups(a, status, sm_count, st);
+    if (!rc) rc = launch_groups(b, status, sm_count, st);
+    return rc;
+}
+
+int dft_tc_launches(const int* Bs, int nsets) {
+    int na = 0, nb = 0;
+    for (int i = 0; i < nsets; ++i) {
+        int B1, B2;
+        dft_factor(Bs[i], &B1, &B2);
+        ++na;
+        if (B2 > 1) ++nb;
+    }
+    return (na + kDftMaxGroups - 1) / kDftMaxGroups + (nb + kDftMaxGroups - 1) / kDftMaxGroups;
 }
 
 }  // namespace sfft4

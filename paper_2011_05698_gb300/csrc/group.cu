@@ -258,7 +258,13 @@ int build_group_plan(sfft4_plan_s* p, int nsig, const int64_t* Ns, const int64_t
             if (d.n > 0) L.decs.push_back(d);
         }
         g->kernels += (int)(L.folds.size() + L.decs.size());
-        for (auto& d : L.dfts) g->kernels += (p->o.precision == SFFT4_BF16X3 && d.B > 64) ? 2 : 1;
+        if (p->o.precision == SFFT4_BF16X3) {
+            std::vector<int> Bs;
+            for (auto& d : L.dfts) Bs.push_back(d.B);
+            g->kernels += dft_tc_launches(Bs.data(), (int)Bs.size());
+        } else {
+            g->kernels += (int)L.dfts.size();
+        }
         g->levels.push_back(L);
     }
     g->kernels += 1;  // finalize
@@ -303,18 +309,24 @@ int group_body(sfft4_plan_s* p, const void* ctx, cudaStream_t st) {
             if (!rc) rc = prof_end(p, st, ev, kProfFold, f.samples);
             if (rc) return rc;
         }
-        for (const auto& d : L.dfts) {
+        if (p->o.precision == SFFT4_BF16X3 && !L.dfts.empty()) {
+            std::vector<DftColSet> sets;
+            for (const auto& d : L.dfts)
+                sets.push_back(DftColSet{d.B, d.w.dA1, d.w.dA2, d.w.tw4, g->zcols + d.off, g->ucols + d.off,
+                                         g->ycols + d.off, d.n});
             cudaEvent_t ev = nullptr;
             rc = prof_begin(p, st, &ev);
-            if (rc) return rc;
-            if (p->o.precision == SFFT4_BF16X3)
-                rc = launch_dft_tc(nullptr, 0, nullptr, nullptr, 0, 0, 1, d.B, d.w.dA1, d.w.dA2, d.w.tw4,
-                                   p->status, p->sm_count, st, g->zcols + d.off, g->ucols + d.off,
-                                   g->ycols + d.off, d.n);
-            else
-                rc = launch_fft_multi(g->zcols + d.off, g->ycols + d.off, d.n, d.B, d.w.tw, st);
+            if (!rc) rc = launch_dft_tc_sets(sets.data(), (int)sets.size(), p->status, p->sm_count, st);
             if (!rc) rc = prof_end(p, st, ev, kProfFft, 0);
             if (rc) return rc;
+        } else {
+            for (const auto& d : L.dfts) {
+                cudaEvent_t ev = nullptr;
+                rc = prof_begin(p, st, &ev);
+                if (!rc) rc = launch_fft_multi(g->zcols + d.off, g->ycols + d.off, d.n, d.B, d.w.tw, st);
+                if (!rc) rc = prof_end(p, st, ev, kProfFft, 0);
+                if (rc) return rc;
+            }
         }
         for (const auto& d : L.decs) {
             cudaEvent_t ev = nullptr;

@@ -320,8 +320,8 @@ __global__ void k_fft(const float2* __restrict__ z, float2* __restrict__ y, int 
 }
 
 // ----------------------------------------------------------------- block helpers ----
-// Exclusive scan of per-thread counts over a 1024-thread block; returns this thread's
-// offset and writes the total to *total (all threads).
+// Exclusive scan of per-thread counts over the block (up to 1024 threads); returns this
+// thread's offset and writes the total to *total (all threads).
 __device__ int block_exscan(int v, int* warp_sums, int* total) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int inc = v;
@@ -333,7 +333,7 @@ __device__ int block_exscan(int v, int* warp_sums, int* total) {
     if (lane == 31) warp_sums[wid] = inc;
     __syncthreads();
     if (wid == 0) {
-        int ws = warp_sums[lane];
+        int ws = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
         int wi = ws;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -392,10 +392,12 @@ __device__ void hash_insert(int32_t* keys, int32_t* vals, int Hlog, int32_t f, i
 
 // ----------------------------------------------------------------- decode -----------
 // Dynamic shared memory of k_decode for B buckets: 26 B bytes of per-bucket arrays, and
-// at least 64 KB for the update's accumulators.
+// for the update's accumulators 64 KB (B <= 512) or 108 KB (B >= 1024: one pass over the
+// found set for up to 6 rounds at B = 1024, 3 at B = 2048).  Two 512-thread CTAs fit on an
+// SM with either.
 __host__ __device__ inline size_t decode_smem(int B) {
     const size_t base = 26 * (size_t)B;
-    const size_t upd = 64 * 1024;  // update accumulators (all rounds at once for small B)
+    const size_t upd = B >= 1024 ? 108 * 1024 : 64 * 1024;
     return base > upd ? base : upd;
 }
 
@@ -819,14 +821,14 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig) 
 }
 
 template <int RMAX>
-__global__ void __launch_bounds__(kDecodeThreads) k_decode(const DecodeArgs a) {
+__global__ void __launch_bounds__(kDecodeThreads, 2) k_decode(const DecodeArgs a) {
     decode_body<RMAX>(a, blockIdx.x);
 }
 
 // Batch of signals with different N and K: CTA b decodes signal jobs[list[b]], whose
 // DecodeArgs already point at that signal's own workspace (so it is signal 0 of its args).
 template <int RMAX>
-__global__ void __launch_bounds__(kDecodeThreads) k_decode_multi(const DecodeArgs* __restrict__ jobs,
+__global__ void __launch_bounds__(kDecodeThreads, 2) k_decode_multi(const DecodeArgs* __restrict__ jobs,
                                                                  const int32_t* __restrict__ list) {
     __shared__ __align__(16) DecodeArgs sa;
     const DecodeArgs* src = jobs + list[blockIdx.x];

@@ -19,7 +19,7 @@ constexpr int kQDen = 256;                    // q = q_n / 256
 constexpr int kBMin = 16;
 constexpr int kBMax = 4096;
 constexpr int kKMax = 4096;
-constexpr int kDecodeThreads = 1024;
+constexpr int kDecodeThreads = 512;     // two decode CTAs per SM
 constexpr int kFoldSmemMax = 100 * 1024;     // staged window rows of one fold CTA
 
 // Rounds [r0, r0 + nr) of one iteration that one fold launch accumulates, and the
@@ -275,6 +275,19 @@ int build_dft_tc_tables(int B, unsigned char* A1, unsigned char* A2, float2* tw4
 int configure_dft_tc();
 int launch_dft_tc(const float2* z, int64_t z_stride, float2* u, float2* y, int64_t y_stride, int nsig,
                   int R, int B, const unsigned char* A1, const unsigned char* A2, const float2* tw4,
-                  int32_t* status, int sm_count, cudaStream_t st, const float2* const* zcols = nullptr,
-                  float2* const* ucols = nullptr, float2* const* ycols = nullptr, int64_t ncols_override = 0);
+                  int32_t* status, int sm_count, cudaStream_t st);
+// Columns of one bucket count within a level of a batch of uneven signals (device tables of
+// per-column z, u and y base pointers).
+struct DftColSet {
+    int B;
+    const unsigned char* A1;
+    const unsigned char* A2;
+    const float2* tw4;
+    const float2* const* zcols;
+    float2* const* ucols;
+    float2* const* ycols;
+    int64_t ncols;
+};
+int launch_dft_tc_sets(const DftColSet* sets, int nsets, int32_t* status, int sm_count, cudaStream_t st);
+int dft_tc_launches(const int* Bs, int nsets);  // launches launch_dft_tc_sets makes
 }  // namespace sfft4
