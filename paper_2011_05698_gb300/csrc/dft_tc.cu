@@ -107,6 +107,7 @@ struct DftGroup {
     const unsigned char* A;        // three bf16 pieces in core-matrix layout
     const float2* tw4;             // stage 2 twiddles (B entries)
     int B, B1, B2, R, P, copies, stage, pad;  // stage 0: single (P = B); 1, 2: four-step
+    int lgP, lgC, lgB1, lgB2;      // log2 of P, copies, B1, B2 (all powers of two)
     int64_t nvec, ngcols, tile0;   // tile0: first tile of this group in the launch's list
 };
 
@@ -140,22 +141,50 @@ __device__ __forceinline__ int group_of(const DftLaunch& L, int64_t ti) {
     return gi;
 }
 
-// Gather the two work items of this thread for tile ti of group g into registers.  A work
-// item is 8 consecutive elements of one input vector; GEMM column n of the tile holds vectors
-// v = (g0 + n) copies + cc, K rows cc 2P + e (re) and cc 2P + P + e (im) hold element e.
+// Work item w of this thread: GEMM column n, vector cc within it, elements e0 .. e0 + 7.  A
+// GEMM column holds vectors v = gc copies + cc; K rows cc 2P + e (re), cc 2P + P + e (im).
+struct DftItem {
+    int n, cc, e0;
+};
+
+__device__ __forceinline__ DftItem dft_item(const DftGroup& g, int item) {
+    DftItem it;
+    it.n = item & (kNT - 1);
+    const int rest = item >> 7;  // kNT = 128
+    it.cc = rest >> (g.lgP - 3);
+    it.e0 = (rest & ((g.P >> 3) - 1)) << 3;
+    return it;
+}
+
+// Gather the two work items of this thread for tile ti of group g into registers (group
+// fields read once into registers before the loads).
 __device__ __forceinline__ void dft_gather(const DftGroup& g, int64_t ti, int tid, float2 (&val)[2][8]) {
-    const int P = g.P, copies = g.copies, B = g.B, B1 = g.B1, B2 = g.B2, R = g.R;
-    const int64_t g0 = (ti - g.tile0) * kNT;
-    const int chunks = P >> 3;
+    const uint32_t g0 = (uint32_t)(ti - g.tile0) * kNT;
+    const int stage = g.stage, lgB1 = g.lgB1, lgB2 = g.lgB2, lgC = g.lgC, lgP = g.lgP;
+    const uint32_t b1m = (uint32_t)g.B1 - 1, b2m = (uint32_t)g.B2 - 1;
+    const uint32_t ngc = (uint32_t)g.ngcols, nv = (uint32_t)g.nvec, Rr = (uint32_t)g.R;
+    const float2* const* __restrict__ icols = g.in_cols;
+    const float2* const ibase = g.in;
+    const int64_t istr = g.in_stride, Bv = g.B;
+    const float2* const __restrict__ tw4 = g.tw4;
+    const int chm = (g.P >> 3) - 1;
 #pragma unroll
     for (int w = 0; w < 2; ++w) {
         const int item = tid + w * kDftThreads;
-        const int n = item % kNT, rest = item / kNT;
-        const int cc = rest / chunks, e0 = (rest - cc * chunks) * 8;
-        const int64_t v = (g0 + n) * copies + cc;
-        if (g0 + n < g.ngcols && v < g.nvec) {
-            if (g.stage == 0) {
-                const float2* cb = g.in_cols ? g.in_cols[v] : g.in + (v / R) * g.in_stride + (v % R) * B;
+        const int n = item & (kNT - 1), rest = item >> 7;
+        const int cc = rest >> (lgP - 3), e0 = (rest & chm) << 3;
+        const uint32_t gc = g0 + n;
+        const uint32_t v = (gc << lgC) + cc;
+        if (gc < ngc && v < nv) {
+            const uint32_t col = stage == 0 ? v : (stage == 1 ? (v >> lgB2) : (v >> lgB1));
+            const float2* cb;
+            if (icols) {
+                cb = icols[col];
+            } else {
+                const uint32_t sg = col / Rr, r = col - sg * Rr;
+                cb = ibase + (int64_t)sg * istr + (int64_t)r * Bv;
+            }
+            if (stage == 0) {
                 const float4* src = (const float4*)(cb + e0);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -163,29 +192,26 @@ __device__ __forceinline__ void dft_gather(const DftGroup& g, int64_t ti, int ti
                     val[w][2 * q] = make_float2(f.x, f.y);
                     val[w][2 * q + 1] = make_float2(f.z, f.w);
                 }
-            } else if (g.stage == 1) {
-                const int64_t col = v / B2;
-                const int j2 = (int)(v - col * B2);
-                const float2* cb = g.in_cols ? g.in_cols[col] : g.in + (col / R) * g.in_stride + (col % R) * B;
+            } else if (stage == 1) {
+                const float2* p = cb + (v & b2m) + ((uint32_t)e0 << lgB2);
 #pragma unroll
-                for (int q = 0; q < 8; ++q) val[w][q] = __ldg(cb + j2 + (int64_t)B2 * (e0 + q));
+                for (int q = 0; q < 8; ++q) val[w][q] = __ldg(p + ((uint32_t)q << lgB2));
             } else {
-                // stage 2 reads the stage-1 output written by the previous launch: plain loads
-                const int64_t col = v / B1;
-                const int k1 = (int)(v - col * B1);
-                const float2* cb = g.in_cols ? g.in_cols[col] : g.in + (col / R) * g.in_stride + (col % R) * B;
-                const float4* src = (const float4*)(cb + (int64_t)k1 * B2 + e0);
+                // stage 2 reads the stage-1 output written by the previous launch
+                const uint32_t k1 = v & b1m;
+                const float4* src = (const float4*)(cb + (k1 << lgB2) + e0);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const float4 f = src[q];
                     val[w][2 * q] = make_float2(f.x, f.y);
                     val[w][2 * q + 1] = make_float2(f.z, f.w);
                 }
+                const float2* tw = tw4 + ((uint32_t)e0 << lgB1) + k1;
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
-                    const float2 tw = __ldg(g.tw4 + (e0 + q) * B1 + k1);
+                    const float2 t = __ldg(tw + ((uint32_t)q << lgB1));
                     const float2 u = val[w][q];
-                    val[w][q] = make_float2(u.x * tw.x - u.y * tw.y, u.x * tw.y + u.y * tw.x);
+                    val[w][q] = make_float2(u.x * t.x - u.y * t.y, u.x * t.y + u.y * t.x);
                 }
             }
         } else {
@@ -198,19 +224,17 @@ __device__ __forceinline__ void dft_gather(const DftGroup& g, int64_t ti, int ti
 // Split the gathered items into the three bf16 X pieces (core-matrix layout).
 __device__ __forceinline__ void dft_store_x(const DftGroup& g, int tid, const float2 (&val)[2][8],
                                             unsigned char* sX) {
-    const int P = g.P, chunks = P >> 3;
 #pragma unroll
     for (int w = 0; w < 2; ++w) {
-        const int item = tid + w * kDftThreads;
-        const int n = item % kNT, rest = item / kNT;
-        const int cc = rest / chunks, e0 = (rest - cc * chunks) * 8;
+        const DftItem it = dft_item(g, tid + w * kDftThreads);
         __align__(16) __nv_bfloat16 re[3][8], imv[3][8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             split3(val[w][q].x, re[0][q], re[1][q], re[2][q]);
             split3(val[w][q].y, imv[0][q], imv[1][q], imv[2][q]);
         }
-        const int ore = core_off(n, cc * 2 * P + e0), oim = core_off(n, cc * 2 * P + P + e0);
+        const int kre = (it.cc << (g.lgP + 1)) + it.e0;
+        const int ore = core_off(it.n, kre), oim = core_off(it.n, kre + g.P);
 #pragma unroll
         for (int pc = 0; pc < 3; ++pc) {
             *(uint4*)(sX + pc * kPieceBytes + ore) = *(const uint4*)re[pc];
@@ -230,6 +254,7 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_dft_bf16x3(const __grid_cons
     unsigned char* sA = sm;                      // 3 pieces of A
     unsigned char* sX = sm + 3 * kPieceBytes;    // 3 pieces of the column tile
     __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t abar;  // completion of the DFT matrix's bulk copy
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5;
     int64_t t_lo, t_hi;
@@ -243,6 +268,7 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_dft_bf16x3(const __grid_cons
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&abar)));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -250,7 +276,7 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_dft_bf16x3(const __grid_cons
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
 
-    uint32_t phase = 0;
+    uint32_t phase = 0, aphase = 0;
     int cur = -1;  // group whose matrix is in sA
     float2 val[2][8];
     int gi = group_of(L, t_lo);
@@ -258,24 +284,60 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_dft_bf16x3(const __grid_cons
     for (int64_t ti = t_lo; ti < t_hi; ++ti) {
         const DftGroup& g = L.g[gi];
         if (gi != cur) {
-            // the previous tile's MMAs have completed, so A may be replaced
-            for (int i = tid; i < 3 * kPieceBytes / 16; i += kDftThreads)
-                ((uint4*)sA)[i] = __ldg((const uint4*)g.A + i);
+            // the previous tile's MMAs have completed, so A may be replaced: one thread
+            // issues bulk copies of the three pieces (TMA), everyone waits on their bytes
+            if (tid == 0) {
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&abar)),
+                             "r"(3 * kPieceBytes));
+#pragma unroll
+                for (int pc = 0; pc < 3; ++pc)
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                            smem_u32(sA + pc * kPieceBytes)),
+                        "l"(g.A + pc * kPieceBytes), "r"(kPieceBytes), "r"(smem_u32(&abar))
+                        : "memory");
+            }
             cur = gi;
+            dft_store_x(g, tid, val, sX);
+            uint32_t adone = 0;
+            for (uint32_t it = 0; it < kWaitLimit && !adone; ++it) {
+                asm volatile(
+                    "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                    " selp.u32 %0, 1, 0, p;\n}"
+                    : "=r"(adone)
+                    : "r"(smem_u32(&abar)), "r"(aphase));
+            }
+            if (!__syncthreads_and(adone)) {
+                // give the copy in flight one more bounded wait before leaving
+                if (tid == 0) atomicExch(L.status, 1);
+                for (uint32_t it = 0, d2 = 0; it < kWaitLimit && !d2; ++it)
+                    asm volatile(
+                        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                        " selp.u32 %0, 1, 0, p;\n}"
+                        : "=r"(d2)
+                        : "r"(smem_u32(&abar)), "r"(aphase));
+                break;
+            }
+            aphase ^= 1u;
+        } else {
+            dft_store_x(g, tid, val, sX);
         }
-        dft_store_x(g, tid, val, sX);
         asm volatile("fence.proxy.async.shared::cta;");
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
         // ---- 8 K-steps x 6 products into the FP32 accumulator --------------------------
         if (tid == 0) {
-            const uint32_t a0 = smem_u32(sA), x0 = smem_u32(sX);
-            const int pa[6] = {0, 0, 1, 0, 1, 2}, px[6] = {0, 1, 0, 2, 1, 0};
+            // descriptors advance by (byte offset >> 4) in their start-address field
+            const uint64_t da = smem_desc(smem_u32(sA)), dx = smem_desc(smem_u32(sX));
+#pragma unroll
             for (int ks = 0; ks < kK / 16; ++ks) {
+#pragma unroll
                 for (int q = 0; q < 6; ++q) {
-                    const uint64_t ad = smem_desc(a0 + pa[q] * kPieceBytes + ks * 256);
-                    const uint64_t bd = smem_desc(x0 + px[q] * kPieceBytes + ks * 256);
+                    const int pa = (q == 2 || q == 4) ? 1 : (q == 5 ? 2 : 0);  // a1x1 a1x2 a2x1 a1x3 a2x2 a3x1
+                    const int px = (q == 1 || q == 4) ? 1 : (q == 3 ? 2 : 0);
+                    const uint64_t ad = da + (uint64_t)((pa * kPieceBytes + ks * 256) >> 4);
+                    const uint64_t bd = dx + (uint64_t)((px * kPieceBytes + ks * 256) >> 4);
                     const uint32_t acc = (ks > 0 || q > 0) ? 1u : 0u;
                     asm volatile(
                         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -326,42 +388,55 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_dft_bf16x3(const __grid_cons
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
         {
-            const int P = g.P, copies = g.copies, B1 = g.B1, B2 = g.B2, R = g.R, B = g.B;
-            const int64_t g0 = (ti - g.tile0) * kNT;
+            // every group field the loop needs is read once into registers: the output stores
+            // go through generic pointers, after which the parameter block would be re-read
+            const uint32_t g0 = (uint32_t)(ti - g.tile0) * kNT;
+            const int P = g.P, lgP = g.lgP, lgC = g.lgC, stage = g.stage;
+            const int lgB1 = g.lgB1, lgB2 = g.lgB2;
+            const uint32_t cm = (uint32_t)g.copies - 1, b1m = (uint32_t)g.B1 - 1, b2m = (uint32_t)g.B2 - 1;
+            const uint32_t ngc = (uint32_t)g.ngcols, nv = (uint32_t)g.nvec, Rr = (uint32_t)g.R;
+            float2* const* __restrict__ ocols = g.out_cols;
+            float2* const obase = g.out;
+            const int64_t ostr = g.out_stride, Bv = g.B;
             // output items (n, cc, k): stage 0 keeps k fastest (contiguous outputs), stages 1-2
             // keep n fastest (consecutive GEMM columns are consecutive output positions)
+#pragma unroll 4
             for (int item = tid; item < kNT * 64; item += kDftThreads) {
                 int n, cc, k;
-                if (g.stage == 0) {
-                    k = item % P;
-                    const int rest = item / P;
-                    cc = rest % copies;
-                    n = rest / copies;
+                if (stage == 0) {
+                    k = item & (P - 1);
+                    const int rest = item >> lgP;
+                    cc = rest & cm;
+                    n = rest >> lgC;
                 } else {
-                    n = item % kNT;
-                    const int rest = item / kNT;
-                    cc = rest / P;
-                    k = rest - cc * P;
+                    n = item & (kNT - 1);
+                    const int rest = item >> 7;
+                    cc = rest >> lgP;
+                    k = rest & (P - 1);
                 }
-                const int64_t gc = g0 + n;
-                const int64_t v = gc * copies + cc;
-                if (gc >= g.ngcols || v >= g.nvec) continue;
-                const float2 o = make_float2(stg[(cc * 2 * P + k) * (kNT + 1) + n],
-                                             stg[(cc * 2 * P + P + k) * (kNT + 1) + n]);
-                int64_t col, off;
-                if (g.stage == 0) {
+                const uint32_t gc = g0 + n;
+                const uint32_t v = (gc << lgC) + cc;
+                if (gc >= ngc || v >= nv) continue;
+                const int kr = (cc << (lgP + 1)) + k;
+                const float2 o = make_float2(stg[kr * (kNT + 1) + n], stg[(kr + P) * (kNT + 1) + n]);
+                uint32_t col, off;
+                if (stage == 0) {
                     col = v;
                     off = k;
-                } else if (g.stage == 1) {
-                    col = v / B2;
-                    const int j2 = (int)(v - col * B2);
-                    off = (int64_t)k * B2 + j2;
+                } else if (stage == 1) {
+                    col = v >> lgB2;
+                    off = ((uint32_t)k << lgB2) + (v & b2m);
                 } else {
-                    col = v / B1;
-                    const int k1 = (int)(v - col * B1);
-                    off = k1 + (int64_t)B1 * k;
+                    col = v >> lgB1;
+                    off = (v & b1m) + ((uint32_t)k << lgB1);
                 }
-                float2* ob = g.out_cols ? g.out_cols[col] : g.out + (col / R) * g.out_stride + (col % R) * B;
+                float2* ob;
+                if (ocols) {
+                    ob = ocols[col];
+                } else {
+                    const uint32_t sg = col / Rr, r = col - sg * Rr;
+                    ob = obase + (int64_t)sg * ostr + (int64_t)r * Bv;
+                }
                 ob[off] = o;
             }
         }
@@ -403,6 +478,12 @@ int configure_dft_tc() {
 
 namespace {
 
+int ilog2i(int v) {
+    int r = 0;
+    while ((1 << r) < v) ++r;
+    return r;
+}
+
 DftGroup make_group(int stage, int B, int P, const unsigned char* A, const float2* tw4, int64_t nvec) {
     DftGroup g;
     memset(&g, 0, sizeof(g));
@@ -415,6 +496,10 @@ DftGroup make_group(int stage, int B, int P, const unsigned char* A, const float
     g.P = P;
     g.copies = 64 / P;
     g.stage = stage;
+    g.lgP = ilog2i(P);
+    g.lgC = ilog2i(g.copies);
+    g.lgB1 = ilog2i(B1);
+    g.lgB2 = ilog2i(B2);
     g.A = A;
     g.tw4 = tw4;
     g.nvec = nvec;

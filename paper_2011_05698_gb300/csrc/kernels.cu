@@ -177,14 +177,29 @@ __device__ __forceinline__ void fold_body(const FoldArgs& a, int slice, int64_t 
         s_par[0] = (uint32_t)s;
         s_par[1] = (uint32_t)o;
     }
-    // stage the window rows of this residue slice
+    // stage the window rows of this residue slice: thread (jj, p) fills column jj of rows
+    // p, p + P, ... of every round, four loads in flight (rows of a warp are coalesced)
     const float* __restrict__ G = a.G;
-    for (int i = tid; i < a.g.nr * Mrows * Wj; i += T) {
-        const int s = i / (Mrows * Wj);
-        const int rem = i - s * Mrows * Wj;
-        const int row = rem / Wj, c = rem - row * Wj;
-        const int gi = rho0 + c + (row + a.mlo[s]) * B - a.tau[s] + a.h;
-        gsm[i] = (gi >= 0 && gi < a.w) ? __ldg(G + gi) : 0.f;
+    if (active) {
+        for (int s = 0; s < a.g.nr; ++s) {
+            const int g0 = rho0 + jj + a.mlo[s] * B - a.tau[s] + a.h;  // G index of row 0
+            float* dst = gsm + (s * Mrows) * Wj + jj;
+            int row = p;
+            for (; row + 3 * P < Mrows; row += 4 * P) {
+                float gv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int gi = g0 + (row + u * P) * B;
+                    gv[u] = (gi >= 0 && gi < a.w) ? __ldg(G + gi) : 0.f;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) dst[(row + u * P) * Wj] = gv[u];
+            }
+            for (; row < Mrows; row += P) {
+                const int gi = g0 + row * B;
+                dst[row * Wj] = (gi >= 0 && gi < a.w) ? __ldg(G + gi) : 0.f;
+            }
+        }
     }
     __syncthreads();
     const uint32_t sigma = s_par[0], aoff = s_par[1], mask = (uint32_t)(a.N - 1);
