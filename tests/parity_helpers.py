@@ -1,0 +1,49 @@
+"""Helpers shared by the GPU parity tests: fragile-decision detection and the replay that
+explains where a GPU run and the oracle part (the oracle's decode, fed the GPU's own bucket
+arrays and found set, must reproduce the GPU at the first iteration where they differ)."""
+
+import numpy as np
+
+from oracle import philox, plan as OP, sfft4 as O, window as OW
+
+FRAGILE_TURNS = 1 << 12      # 2^-20 turns: FP32 phases of FP32 buckets resolve ~100 units
+FRAGILE_REL = 1e-5           # relative margin of magnitude and selection decisions
+
+
+def fragile(tr):
+    """True when a decision of this oracle iteration sits within a fragile margin."""
+    if tr["sel_margin"] < FRAGILE_REL:
+        return True
+    loc = tr["loc"]
+    return loc is not None and (np.any(loc["margin"] < FRAGILE_TURNS) or np.any(loc["mag_margin"] < FRAGILE_REL))
+
+
+def found_set_from(f, v, vt):
+    fs = O.FoundSet()
+    for fi, vi, vo in zip(f, v, vt):
+        fs.merge(int(fi), complex(vi), int(vo), 0)
+    return fs
+
+
+def explain_divergence(p, r, N, K, l, q, seed, B1=0):
+    """Walk the iterations of the GPU trace (plan made with trace=True, signal 0) and the
+    oracle trace; at the first iteration whose found sets differ, the oracle must have had a
+    fragile decision and its decode fed the GPU's own buckets must reproduce the GPU's found
+    set.  Returns that iteration (or None when the traces never part)."""
+    op = OP.make_plan(N, K, l, q, seed=seed, B1=B1)
+    wc = OW.WindowCache(N, op.delta)
+    prev = O.FoundSet()
+    for tr in r["traces"]:
+        Y, f, v, vt = p.trace(tr["m"])
+        fo = tr["found_after"]
+        if list(fo.f) == [int(x) for x in f]:
+            prev = found_set_from(f, v, vt)
+            continue
+        assert fragile(tr), ("divergence without a fragile margin", tr["m"])
+        it = op.iters[tr["m"] - 1]
+        sigma, a = philox.permutation_draw(seed, 0, it.m, N)
+        _, _, Ghat = wc.get(it.B)
+        out, _ = O.decode_iteration(Y.astype(np.complex128), prev, it, op, sigma, a, r["theta"], Ghat)
+        assert list(out.f) == [int(x) for x in f], ("replay does not reproduce the GPU", tr["m"])
+        return tr["m"]
+    return None

@@ -14,6 +14,8 @@ import pytest
 from oracle import philox, plan as OP, sfft4 as O, window as OW
 from synth import sparse_signal
 
+import parity_helpers as PH
+
 pytestmark = pytest.mark.gpu
 
 CONFIGS = {
@@ -140,10 +142,6 @@ def test_bucketize_parity_other_signal_index(s4):
     bucket_parity(s4, N, K, l, q, B1, seed=5, snr=None, ms=[1], signal=37)
 
 
-FRAGILE_TURNS = 1 << 12      # 2^-20 turns: FP32 phases of FP32 buckets resolve ~100 units
-FRAGILE_REL = 1e-5           # relative margin of magnitude and selection decisions
-
-
 def e2e(s4, name, seed, snr=None, trace=False, precision="fp32"):
     N, K, l, q, B1 = CONFIGS[name]
     sig = sparse_signal(N, K, seed, snr)
@@ -155,37 +153,9 @@ def e2e(s4, name, seed, snr=None, trace=False, precision="fp32"):
     return sig, g, r, p
 
 
-def fragile(tr):
-    """True when a decision of this oracle iteration sits within a fragile margin."""
-    if tr["sel_margin"] < FRAGILE_REL:
-        return True
-    loc = tr["loc"]
-    return loc is not None and (np.any(loc["margin"] < FRAGILE_TURNS) or np.any(loc["mag_margin"] < FRAGILE_REL))
-
-
 def explain_divergence(p, r, name, seed):
-    """Walk the iterations of the GPU trace and the oracle trace; at the first iteration
-    whose found sets differ, the oracle must have had a fragile decision and the oracle's
-    decode fed the GPU's own buckets must reproduce the GPU's found set.  Returns the
-    iteration index (or None when the traces never part)."""
     N, K, l, q, B1 = CONFIGS[name]
-    op = oracle_plan(N, K, l, q, seed, B1)
-    wc = OW.WindowCache(N, op.delta)
-    prev = O.FoundSet()
-    for tr in r["traces"]:
-        Y, f, v, vt = p.trace(tr["m"])
-        fo = tr["found_after"]
-        if list(fo.f) == [int(x) for x in f]:
-            prev = found_set_from(f, v, vt)
-            continue
-        assert fragile(tr), ("divergence without a fragile margin", tr["m"])
-        it = op.iters[tr["m"] - 1]
-        sigma, a = philox.permutation_draw(seed, 0, it.m, N)
-        _, _, Ghat = wc.get(it.B)
-        out, _ = O.decode_iteration(Y.astype(np.complex128), prev, it, op, sigma, a, r["theta"], Ghat)
-        assert list(out.f) == [int(x) for x in f], ("replay does not reproduce the GPU", tr["m"])
-        return tr["m"]
-    return None
+    return PH.explain_divergence(p, r, N, K, l, q, seed, B1)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
@@ -220,13 +190,6 @@ def test_end_to_end_noisy_support_and_values(s4):
     assert rel <= 1e-4
 
 
-def found_set_from(f, v, vt):
-    fs = O.FoundSet()
-    for fi, vi, vo in zip(f, v, vt):
-        fs.merge(int(fi), complex(vi), int(vo), 0)
-    return fs
-
-
 @pytest.mark.parametrize("name,seed,snr", [("c2", 0, 20.0), ("c2", 1, None), ("c1", 2, 20.0)])
 def test_replay_decode_parity(s4, name, seed, snr):
     """Each iteration's decode (update, selection, location, votes, estimate, merge) of the
@@ -251,19 +214,15 @@ def test_replay_decode_parity(s4, name, seed, snr):
         out, tr = O.decode_iteration(Y, prev, it, op, sigma, a, theta, Ghat)
         if list(out.f) != [int(x) for x in f]:
             # allowed only when a decision of this iteration sits on a fragile margin
-            loc = tr["loc"]
-            fragile = tr["sel_margin"] < 1e-5
-            if loc is not None:
-                fragile = fragile or np.any(loc["margin"] < 4096) or np.any(loc["mag_margin"] < 1e-5)
-            assert fragile, (it.m, set(out.f) ^ set(int(x) for x in f))
+            assert PH.fragile(tr), (it.m, set(out.f) ^ set(int(x) for x in f))
             fragile_total += 1
-            prev = found_set_from(f, v, vt)
+            prev = PH.found_set_from(f, v, vt)
             continue
         assert [int(x) for x in vt] == list(out.votes)
         vo = np.asarray(out.v)
         if vo.size:
             assert np.linalg.norm(vo - v) <= 1e-4 * np.linalg.norm(vo) + 1e-12
-        prev = found_set_from(f, v, vt)
+        prev = PH.found_set_from(f, v, vt)
     assert fragile_total <= 1
     p.close()
 
