@@ -190,7 +190,21 @@ def uneven_form(s4, args, dev, stream, dist):
     Ns, Ks, snrs = uneven_sizes(nsig, seed)
     xs = [device_signal(int(Ns[i]), int(Ks[i]), signal_seed(seed, i), snrs[i], dev)[0] for i in range(nsig)]
     graph = not args.no_graph
-    bp = s4.BatchPlan(Ns.tolist(), Ks.tolist(), L_DEF, Q_DEF, seed=seed, precision=args.precision, graph=graph)
+    B1s, tune = None, None
+    if not args.no_autotune:
+        import collections
+        import tempfile
+        from paper_2011_05698_gb300 import autotune
+        cache = os.path.join(tempfile.gettempdir(), "sfft4_autotune_bench.json")
+        B1s = autotune.choose_b1(Ns.tolist(), Ks.tolist(), L_DEF, Q_DEF, precision=args.precision,
+                                 cache_path=cache, device=dev)
+        ratio = collections.Counter()
+        for b, k in zip(B1s, Ks.tolist()):
+            ratio[f"{b / autotune._pow2ceil(2 * k):g}" if b else "default"] += 1
+        tune = {"seconds": autotune.choose_b1.last_seconds, "cache": cache,
+                "B1_over_pow2ceil_2K": dict(ratio)}
+    bp = s4.BatchPlan(Ns.tolist(), Ks.tolist(), L_DEF, Q_DEF, seed=seed, precision=args.precision, graph=graph,
+                      B1s=B1s)
     out = bp.outputs()
     ptrs = bp.pointers(xs)
 
@@ -206,7 +220,8 @@ def uneven_form(s4, args, dev, stream, dist):
     world = dist.get_world_size() if dist is not None else 1
     info = dict(bp.info)
     bp.close()
-    bq = s4.BatchPlan(Ns.tolist(), Ks.tolist(), L_DEF, Q_DEF, seed=seed, precision=args.precision, profile=True)
+    bq = s4.BatchPlan(Ns.tolist(), Ks.tolist(), L_DEF, Q_DEF, seed=seed, precision=args.precision, profile=True,
+                      B1s=B1s)
     outq = bq.outputs()
     bq.execute(xs, out=outq)
     torch.cuda.synchronize()
@@ -221,8 +236,123 @@ def uneven_form(s4, args, dev, stream, dist):
             "graph_launches_per_step": 1 if graph else 0, "levels": info["n_levels"], "classes": info["n_classes"],
             "workload": "512 signals: N=2^n, n uniform on 16..22; K=round(exp U[ln 10, ln 2000]) <= N/64; "
                         "SNR U[10, 40] dB; l=16, q=1",
-            "fold_gbs_useful": fold_gbs,
+            "fold_gbs_useful": fold_gbs, "autotune": tune,
             "kernel_ms_one_execute": {k: prof[k + "_ms"] for k in ("fold", "fft", "decode", "finalize")}}
+
+
+def configs_form(s4, args, dev, stream):
+    """The small single-signal configurations over 10 seeds each: N = 2^14, K = 16 (l = 4,
+    q = 0.5, B1 = 64, noiseless) and N = 2^20, K = 100 (l = 16, q = 1, B1 = 128, 20 dB), plus
+    N = 2^22, K = 1000 at 20 dB: plain FP32 form (one execute per signal), batched BF16x3 form
+    (the 10 seeds in one execute, and 256 signals per execute for throughput), exact-support
+    rate and error against the generator, samples per transform."""
+    import numpy as np
+    import torch
+    from synth.signals import device_signal
+    cfgs = [("N=2^14 K=16 l=4 q=0.5 B1=64 noiseless", 2**14, 16, 4, 0.5, 64, None),
+            ("N=2^20 K=100 l=16 q=1 B1=128 20 dB", 2**20, 100, 16, 1.0, 128, 20.0),
+            ("N=2^22 K=1000 l=16 q=1 20 dB", 2**22, 1000, 16, 1.0, 0, 20.0)]
+    out_rows = []
+    for name, N, K, l, q, B1, snr in cfgs:
+        S = 10
+        xs = torch.empty((S, N), dtype=torch.complex64, device=dev)
+        truth = [device_signal(N, K, 3000 + i, snr, dev, out=xs[i])[1:] for i in range(S)]
+        row = {"config": name, "seeds": S}
+        for form, prec in (("plain_fp32", "fp32"), ("batched_bf16x3", "bf16x3")):
+            p = s4.Plan(N, K, l, q, seed=21, B1=B1, max_batch=256, precision=prec)
+            if form == "plain_fp32":
+                res = [p._outputs(1) for _ in range(S)]
+
+                def fn():
+                    for i in range(S):
+                        p.execute(xs[i], res[i])
+                el = timed(fn, 5, 2, stream, None)
+                got = [(r[0][0, :int(r[2][0])].cpu().numpy(), r[1][0, :int(r[2][0])].cpu().numpy()) for r in res]
+                tps = S * 5 / el
+            else:
+                o = p._outputs(S)
+                el = timed(lambda: p.execute_batched(xs, o), 5, 2, stream, None)
+                idx, val, nf = o[0].cpu().numpy(), o[1].cpu().numpy(), o[2].cpu().numpy()
+                got = [(idx[i, :nf[i]], val[i, :nf[i]]) for i in range(S)]
+                tps = S * 5 / el
+                big = xs.repeat((256 + S - 1) // S, 1)[:256].contiguous()
+                ob = p._outputs(256)
+                eb = timed(lambda: p.execute_batched(big, ob), 5, 2, stream, None)
+                row["batched_bf16x3_256_per_execute"] = {"transforms_per_s": 256 * 5 / eb}
+                del big
+            ok, errs = 0, []
+            for (fi, vi), (ft, vt) in zip(got, truth):
+                ok += int(np.array_equal(fi, ft))
+                est = dict(zip(fi.tolist(), vi.tolist()))
+                tru = dict(zip(ft.tolist(), vt.tolist()))
+                allf = sorted(set(est) | set(tru))
+                errs.append(sum(abs(est.get(f, 0) - tru.get(f, 0)) for f in allf) / K)
+            row[form] = {"transforms_per_s": tps, "exact_support_rate": ok / S, "l1_error_mean": float(np.mean(errs)),
+                         "samples_per_transform": p.info["samples_per_transform"],
+                         "samples_frac_of_N": p.info["samples_per_transform"] / N, "iterations": p.info["n_iters"]}
+            p.close()
+        out_rows.append(row)
+    return {"form": "configs", "data": "synthetic", "rows": out_rows}
+
+
+def sweep_form(s4, args, dev, stream):
+    """Large-N sweep: N = 2^26, K = 4000, SNR in {0, 10, 20, 30, 40} dB, l in {4, 8, 16, 32} x
+    q in {0.5, 1, 1.5, 2}; per point: runtime of the batched split-precision form (one execute
+    of all seeds) and of the plain FP32 form (one execute per signal), samples touched, and
+    exact-support success and L1 error of both over the seeds."""
+    import numpy as np
+    import torch
+    from synth.signals import device_signal
+    N, K, S = 2**26, 4000, args.sweep_seeds
+    xs = torch.empty((S, N), dtype=torch.complex64, device=dev)
+    supp = []
+    rows = []
+    for snr in (0.0, 10.0, 20.0, 30.0, 40.0):
+        supp = []
+        for i in range(S):
+            _, f, v = device_signal(N, K, 9000 + i, snr, dev, out=xs[i])
+            supp.append((f, v))
+        for l in (4, 8, 16, 32):
+            for q in (0.5, 1.0, 1.5, 2.0):
+                row = {"snr_db": snr, "l": l, "q": q}
+                for form, prec, batched in (("batched_bf16x3", "bf16x3", True), ("plain_fp32", "fp32", False)):
+                    p = s4.Plan(N, K, l, q, seed=77, max_batch=S if batched else 1, precision=prec)
+                    if batched:
+                        out = p._outputs(S)
+                        fn = (lambda: p.execute_batched(xs, out))
+                    else:
+                        out1 = p._outputs(1)
+                        res = [p._outputs(1) for _ in range(S)]
+
+                        def fn():
+                            for i in range(S):
+                                p.execute(xs[i], res[i])
+                    el = timed(fn, 3, 1, stream, None)
+                    if batched:
+                        idx, val, nf = out[0].cpu().numpy(), out[1].cpu().numpy(), out[2].cpu().numpy()
+                        got = [(idx[i, :nf[i]], val[i, :nf[i]]) for i in range(S)]
+                    else:
+                        got = [(r[0][0, :int(r[2][0])].cpu().numpy(), r[1][0, :int(r[2][0])].cpu().numpy()) for r in res]
+                        del out1
+                    ok, l1 = 0, []
+                    for (fi, vi), (ft, vt) in zip(got, supp):
+                        ok += int(np.array_equal(fi, ft))
+                        allf = np.union1d(fi, ft)
+                        est = dict(zip(fi.tolist(), vi.tolist()))
+                        tru = dict(zip(ft.tolist(), vt.tolist()))
+                        l1.append(sum(abs(est.get(f, 0) - tru.get(f, 0)) for f in allf.tolist()) / K)
+                    row[form] = {"ms_per_transform": 1e3 * el / 3 / S, "success": ok / S,
+                                 "l1_error_mean": float(np.mean(l1)),
+                                 "samples_per_transform": p.info["samples_per_transform"],
+                                 "samples_frac_of_N": p.info["samples_per_transform"] / N,
+                                 "iterations": p.info["n_iters"]}
+                    p.close()
+                rows.append(row)
+    return {"form": "large_n_sweep", "N": N, "K": K, "seeds": S, "data": "synthetic",
+            "workload": "N=2^26 K=4000 unit-magnitude uniform-phase spectra, time-domain noise at the "
+                        "stated SNR; plain form: one sfft4_execute per signal (Philox signal 0); "
+                        "batched form: one sfft4_execute_batched of all seeds",
+            "rows": rows}
 
 
 def timed(fn, steps, warmup, stream, dist=None):
@@ -259,9 +389,12 @@ def main():
     ap.add_argument("--plain-signals", type=int, default=16)
     ap.add_argument("--uneven-signals", type=int, default=512)
     ap.add_argument("--no-fp32-form", action="store_true")
-    ap.add_argument("--form", default="all", choices=["all", "uneven"],
-                    help="uneven: time only the uneven-batch form and print its line")
+    ap.add_argument("--form", default="all", choices=["all", "uneven", "sweep", "configs"],
+                    help="uneven: time only the uneven-batch form; sweep: the large-N SNR x (l, q) "
+                         "sweep (N = 2^26, K = 4000, 10 seeds)")
+    ap.add_argument("--sweep-seeds", type=int, default=10)
     ap.add_argument("--no-graph", action="store_true", help="uneven form without CUDA-graph replay")
+    ap.add_argument("--no-autotune", action="store_true", help="uneven form with the default B1 per signal")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -289,6 +422,20 @@ def main():
     from paper_2011_05698_gb300 import build
     build.build()
     import paper_2011_05698_gb300 as s4
+
+    if args.form == "configs":
+        if rank == 0:
+            print(json.dumps(configs_form(s4, args, dev, torch.cuda.current_stream(dev))), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    if args.form == "sweep":
+        if rank == 0:
+            print(json.dumps(sweep_form(s4, args, dev, torch.cuda.current_stream(dev))), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
 
     if args.form == "uneven":
         u = uneven_form(s4, args, dev, torch.cuda.current_stream(dev), dist)

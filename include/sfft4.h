@@ -140,8 +140,10 @@ SFFT4_API int sfft4_execute_batched(sfft4_plan_t plan, int32_t nsig, const void*
  * sfft4_plan_batched -- plan of nsig transforms of different sizes, executed together
  * (batch of independent problems; each signal follows its own static schedule of Section 3.1).
  *   N[i], K[i]  size and sparsity of signal i, each within sfft4_plan's limits
+ *   B1          NULL, or nsig first-iteration bucket counts (0 = the default of that signal;
+ *               e.g. chosen per (N, K) by an autotuner); overrides opts->B1
  *   l, q, seed, opts  as for sfft4_plan, shared by every signal (opts.max_batch is ignored)
- * Signals with equal (N, K) share one schedule; window tables are shared by (N, B).  Level m
+ * Signals with equal (N, K, B1) share one schedule; window tables are shared by (N, B).  Level m
  * of an execute runs iteration m of every signal that has one, as one fold launch per
  * rounds-per-group count, one DFT launch per bucket count and one decode launch per
  * round-count class, taking their work from job tables built here.  Signal i uses Philox
@@ -149,7 +151,7 @@ SFFT4_API int sfft4_execute_batched(sfft4_plan_t plan, int32_t nsig, const void*
  * Errors: SFFT4_EINVAL (NULL pointers, nsig < 1, any size invalid), SFFT4_ENOMEM, SFFT4_ECUDA.
  */
 SFFT4_API int sfft4_plan_batched(sfft4_plan_t* out, int32_t nsig, const int64_t* N, const int64_t* K,
-                                 int32_t l, double q, uint64_t seed, const sfft4_opts* opts);
+                                 const int32_t* B1, int32_t l, double q, uint64_t seed, const sfft4_opts* opts);
 
 /*
  * sfft4_execute_batched_v -- execute a plan from sfft4_plan_batched.
@@ -168,7 +170,7 @@ SFFT4_API int sfft4_execute_batched_v(sfft4_plan_t plan, const void* const* x_pt
 
 typedef struct {
     int32_t nsig;
-    int32_t n_classes;          /* distinct (N, K) */
+    int32_t n_classes;          /* distinct (N, K, B1) */
     int32_t n_levels;           /* longest schedule */
     int32_t kernels_per_execute;
     int64_t Kmax;               /* output row length */

@@ -211,9 +211,10 @@ class Plan:
 class BatchPlan:
     """Plan of a batch of signals of different sizes N_i and sparsities K_i, executed together
     (each signal follows its own static schedule, Section 3.1; signal i uses Philox counter
-    (i, m, 0, 0)).  Outputs are rows of length Kmax = max K_i."""
+    (i, m, 0, 0)).  Outputs are rows of length Kmax = max K_i.  B1s optionally gives each
+    signal's first-iteration bucket count (0 = default), e.g. from `autotune.choose_b1`."""
 
-    def __init__(self, Ns, Ks, l=16, q=1.0, seed=0, *, B1=0, delta=1e-8, precision="fp32",
+    def __init__(self, Ns, Ks, l=16, q=1.0, seed=0, *, B1=0, B1s=None, delta=1e-8, precision="fp32",
                  min_votes=0, select_factor=2.0, sig_floor=1e-10, mag_tol=0.5, max_iters=64,
                  profile=False, graph=False, device=None):
         import torch
@@ -228,9 +229,14 @@ class BatchPlan:
         nsig = len(Ns)
         Na = (ctypes.c_int64 * nsig)(*Ns)
         Ka = (ctypes.c_int64 * nsig)(*Ks)
+        Ba = None
+        if B1s is not None:
+            if len(B1s) != nsig:
+                raise ValueError("B1s must have one entry per signal")
+            Ba = (ctypes.c_int32 * nsig)(*[int(b) for b in B1s])
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
-            check(lib.sfft4_plan_batched(ctypes.byref(h), nsig, Na, Ka, l, q, seed, ctypes.byref(o)),
+            check(lib.sfft4_plan_batched(ctypes.byref(h), nsig, Na, Ka, Ba, l, q, seed, ctypes.byref(o)),
                   "sfft4_plan_batched")
         self._h = h
         self.Ns, self.Ks, self.l, self.q, self.seed = Ns, Ks, l, q, seed

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <map>
 #include <new>
+#include <tuple>
 
 #include "sfft4_internal.cuh"
 
@@ -104,21 +105,25 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 void destroy_group(Group* g) { free_group(g); }
 
-int build_group_plan(sfft4_plan_s* p, int nsig, const int64_t* Ns, const int64_t* Ks, int32_t l,
-                     double q, uint64_t seed, const sfft4_opts* opts) {
+int build_group_plan(sfft4_plan_s* p, int nsig, const int64_t* Ns, const int64_t* Ks, const int32_t* B1s,
+                     int32_t l, double q, uint64_t seed, const sfft4_opts* opts) {
     Group* g = new (std::nothrow) Group();
     if (!g) return SFFT4_ENOMEM;
     p->grp = g;
     g->nsig = nsig;
-    // classes of equal (N, K), each with its own static schedule
-    std::map<std::pair<int64_t, int64_t>, int> cls_of;
+    // classes of equal (N, K, B1), each with its own static schedule
+    std::map<std::tuple<int64_t, int64_t, int32_t>, int> cls_of;
     for (int i = 0; i < nsig; ++i) {
-        auto key = std::make_pair(Ns[i], Ks[i]);
+        sfft4_opts oi;
+        if (opts) oi = *opts;
+        else sfft4_opts_default(&oi);
+        if (B1s) oi.B1 = B1s[i];
+        auto key = std::make_tuple(Ns[i], Ks[i], oi.B1);
         auto itc = cls_of.find(key);
         if (itc == cls_of.end()) {
             sfft4_opts o;
             int qn = 0;
-            int rc = plan_options(Ns[i], Ks[i], l, q, opts, &o, &qn);
+            int rc = plan_options(Ns[i], Ks[i], l, q, &oi, &o, &qn);
             if (rc) return rc;
             sfft4_plan_s* c = new (std::nothrow) sfft4_plan_s();
             if (!c) return SFFT4_ENOMEM;

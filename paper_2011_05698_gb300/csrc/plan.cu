@@ -415,15 +415,19 @@ int sfft4_plan(sfft4_plan_t* out, int64_t N, int64_t K, int32_t l, double q, uin
     return SFFT4_OK;
 }
 
-int sfft4_plan_batched(sfft4_plan_t* out, int32_t nsig, const int64_t* N, const int64_t* K, int32_t l,
-                       double q, uint64_t seed, const sfft4_opts* opts) {
+int sfft4_plan_batched(sfft4_plan_t* out, int32_t nsig, const int64_t* N, const int64_t* K, const int32_t* B1,
+                       int32_t l, double q, uint64_t seed, const sfft4_opts* opts) {
     if (!out) return SFFT4_EINVAL;
     *out = nullptr;
     if (nsig < 1 || !N || !K) return SFFT4_EINVAL;
     sfft4_opts o;
     int qn = 0;
     for (int32_t i = 0; i < nsig; ++i) {
-        int rc0 = plan_options(N[i], K[i], l, q, opts, &o, &qn);
+        sfft4_opts oi;
+        if (opts) oi = *opts;
+        else sfft4_opts_default(&oi);
+        if (B1) oi.B1 = B1[i];
+        int rc0 = plan_options(N[i], K[i], l, q, &oi, &o, &qn);
         if (rc0) return rc0;
     }
     sfft4_plan_s* p = new (std::nothrow) sfft4_plan_s();
@@ -439,7 +443,7 @@ int sfft4_plan_batched(sfft4_plan_t* out, int32_t nsig, const int64_t* N, const 
         CK(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, o.l2_fetch_bytes ? o.l2_fetch_bytes : 32));
     CK(cudaMalloc(&p->status, sizeof(int32_t)));
     CK(cudaMemset(p->status, 0, sizeof(int32_t)));
-    int rc = build_group_plan(p, nsig, N, K, l, q, seed, opts);
+    int rc = build_group_plan(p, nsig, N, K, B1, l, q, seed, opts);
     if (rc) { free_plan(p); return rc; }
     CK(cudaDeviceSynchronize());
     *out = p;

@@ -261,8 +261,8 @@ int check_cuda(cudaError_t e);
 int graph_run(sfft4_plan_s* p, const uint64_t key[8], cudaStream_t st, int (*body)(sfft4_plan_s*, const void*, cudaStream_t),
               const void* ctx);
 // Implemented in group.cu.
-int build_group_plan(sfft4_plan_s* p, int nsig, const int64_t* N, const int64_t* K, int32_t l, double q,
-                     uint64_t seed, const sfft4_opts* opts);
+int build_group_plan(sfft4_plan_s* p, int nsig, const int64_t* N, const int64_t* K, const int32_t* B1, int32_t l,
+                     double q, uint64_t seed, const sfft4_opts* opts);
 void destroy_group(Group* g);
 // Implemented in plan.cu.
 int plan_options(int64_t N, int64_t K, int32_t l, double q, const sfft4_opts* opts, sfft4_opts* out,

@@ -127,13 +127,17 @@ def test_plan_batched_rejects_invalid_sizes(lib):
 
     # one bad signal anywhere in the batch rejects the whole plan, before any device work
     for Ns, Ks in [([2**14, 1000], [16, 4]), ([2**14, 2**16], [16, 0]), ([2**14], [300])]:
-        assert lib.sfft4_plan_batched(ctypes.byref(h), len(Ns), arr(Ns), arr(Ks), 16, 1.0, 0, None) \
+        assert lib.sfft4_plan_batched(ctypes.byref(h), len(Ns), arr(Ns), arr(Ks), None, 16, 1.0, 0, None) \
             == _lib.SFFT4_EINVAL
         assert not h.value
-    assert lib.sfft4_plan_batched(ctypes.byref(h), 0, arr([2**14]), arr([16]), 16, 1.0, 0, None) \
+    assert lib.sfft4_plan_batched(ctypes.byref(h), 0, arr([2**14]), arr([16]), None, 16, 1.0, 0, None) \
         == _lib.SFFT4_EINVAL
-    assert lib.sfft4_plan_batched(ctypes.byref(h), 1, None, None, 16, 1.0, 0, None) == _lib.SFFT4_EINVAL
-    assert lib.sfft4_plan_batched(None, 1, arr([2**14]), arr([16]), 16, 1.0, 0, None) == _lib.SFFT4_EINVAL
+    assert lib.sfft4_plan_batched(ctypes.byref(h), 1, None, None, None, 16, 1.0, 0, None) == _lib.SFFT4_EINVAL
+    assert lib.sfft4_plan_batched(None, 1, arr([2**14]), arr([16]), None, 16, 1.0, 0, None) == _lib.SFFT4_EINVAL
+    # a per-signal B1 that is not a power of two, or whose window is wider than N/2
+    b1 = (ctypes.c_int32 * 2)(0, 48)
+    assert lib.sfft4_plan_batched(ctypes.byref(h), 2, arr([2**14, 2**14]), arr([16, 16]), b1, 16, 1.0, 0, None) \
+        == _lib.SFFT4_EINVAL
 
 
 def test_binding_fails_loudly_without_cuda():
@@ -143,3 +147,11 @@ def test_binding_fails_loudly_without_cuda():
     import paper_2011_05698_gb300 as s4
     with pytest.raises(RuntimeError):
         s4.Plan(2**14, 16, 4, 0.5)
+
+
+def test_autotune_candidates():
+    from paper_2011_05698_gb300 import autotune
+    assert autotune.candidates(2**22, 1000) == [512, 1024, 2048, 4096]
+    assert autotune.candidates(2**16, 600) == [512, 1024]          # capped at N/64
+    assert autotune.candidates(2**14, 4) == [16]                   # floor at 16
+    assert all(b & (b - 1) == 0 for b in autotune.candidates(2**20, 77))
