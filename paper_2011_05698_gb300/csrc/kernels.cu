@@ -31,15 +31,39 @@ __device__ __forceinline__ float2 ld_stream(const float2* p) {
 // (cos, sin) of 2 pi r / 2^n for 0 <= r < 2^n, with exactly representable sincospif
 // arguments: r = rh 2^12 + rl, angle = 2 pi rh / 2^(n-12) + 2 pi rl / 2^n.
 __device__ __forceinline__ float2 cis_2pi_frac(uint64_t r, int n) {
+    // r < 2^n <= 2^30: 32-bit conversions (64-bit integer conversions run at the FP64 rate)
+    const uint32_t r32 = (uint32_t)r;
     float s, c;
     if (n <= 24) {
-        sincospif(ldexpf((float)r, 1 - n), &s, &c);
+        sincospif(ldexpf((float)r32, 1 - n), &s, &c);
         return make_float2(c, s);
     }
     float sa, ca, sb, cb;
-    sincospif(ldexpf((float)(r >> 12), 13 - n), &sa, &ca);
-    sincospif(ldexpf((float)(r & 4095u), 1 - n), &sb, &cb);
+    sincospif(ldexpf((float)(r32 >> 12), 13 - n), &sa, &ca);
+    sincospif(ldexpf((float)(r32 & 4095u), 1 - n), &sb, &cb);
     return make_float2(ca * cb - sa * sb, sa * cb + ca * sb);
+}
+
+// rint(x) as int64 (round half to even, as __float2ll_rn) with 32-bit conversions: for
+// |x| < 2^47, x = h 2^24 + d with h = rint(x / 2^24) and d exact (one fmaf), and
+// rint(x) = h 2^24 + rint(d) because h 2^24 is an even integer.
+// Out-of-range cases call the 64-bit conversion in a separate function, so that the
+// compiler cannot if-convert it into every lane.
+__device__ __noinline__ long long f2ll_rn_wide(float x) { return __float2ll_rn(x); }
+__device__ __noinline__ float ll2f_rn_wide(long long v) { return __ll2float_rn(v); }
+
+__device__ __forceinline__ long long f2ll_rn(float x) {
+    if (!(fabsf(x) < 0x1p47f)) return f2ll_rn_wide(x);
+    const int h = __float2int_rn(x * 0x1p-24f);
+    const float d = fmaf(-(float)h, 0x1p24f, x);
+    return ((long long)h << 24) + __float2int_rn(d);
+}
+
+// The float nearest to v (ties to even, as __ll2float_rn): for |v| < 2^48, v = h 2^24 + l
+// with 0 <= l < 2^24, both exact in float, and one rounding in fmaf.
+__device__ __forceinline__ float ll2f_rn(long long v) {
+    if (v >= (1ll << 48) || v <= -(1ll << 48)) return ll2f_rn_wide(v);
+    return fmaf((float)(int)(v >> 24), 0x1p24f, (float)(int)(v & 0xFFFFFF));
 }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -165,7 +189,7 @@ template <int RG>
 __device__ __forceinline__ void fold_body(const FoldArgs& a, int slice, int64_t signal_index,
                                           const float2* __restrict__ x, float2* zsig, float* gsm,
                                           uint32_t* s_par, float2* red) {
-    const int tid = threadIdx.x, T = blockDim.x;
+    const int tid = threadIdx.x;
     const int Wj = a.Wj, B = a.B, Mrows = a.Mrows;
     const int P = a.g.P;
     const bool active = tid < Wj * P;  // a launch may carry more threads than this job uses
@@ -406,13 +430,17 @@ __device__ void hash_insert(int32_t* keys, int32_t* vals, int Hlog, int32_t f, i
 }
 
 // ----------------------------------------------------------------- decode -----------
-// Dynamic shared memory of k_decode for B buckets: 26 B bytes of per-bucket arrays, and
-// for the update's accumulators 64 KB (B <= 512) or 108 KB (B >= 1024: one pass over the
-// found set for up to 6 rounds at B = 1024, 3 at B = 2048).  Two 512-thread CTAs fit on an
-// SM with either.
+constexpr int kUpdRounds = 4;  // rounds per pass of the gather update (int64 accumulators in registers)
+// Largest B updated in gather form: with many found entries per bucket (small B) the gather
+// avoids conflicting atomics; with few (B >= 1024) the scatter's single pass over the found
+// set is shorter (phase timing on a GB300: 28 vs 41 us at B = 2048, 34 vs 40 us at B = 256).
+constexpr int kGatherMaxB = 512;
+// Dynamic shared memory of k_decode for B buckets: 26 B bytes of per-bucket arrays, and at
+// least 108 KB for the update (staged found entries, 24 B each, or accumulator copies).  Two
+// 512-thread CTAs fit on an SM.
 __host__ __device__ inline size_t decode_smem(int B) {
     const size_t base = 26 * (size_t)B;
-    const size_t upd = B >= 1024 ? 108 * 1024 : 64 * 1024;
+    const size_t upd = 108 * 1024;
     return base > upd ? base : upd;
 }
 
@@ -466,7 +494,7 @@ __device__ __forceinline__ uint32_t phase_fixed(float2 ys, float2 y0) {
     const float cr = ys.x * y0.x + ys.y * y0.y;
     const float cim = ys.y * y0.x - ys.x * y0.y;
     const float turns = atan2f(cim, cr) * 0.15915494309189535f;
-    return (uint32_t)__float2ll_rn(turns * 4294967296.0f);
+    return (uint32_t)f2ll_rn(turns * 4294967296.0f);
 }
 
 // Radix select over 32-bit keys held one chunk per thread: returns the value T of the
@@ -583,67 +611,205 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig) 
     // ---- 1. update: yhat' = yhat - yhat_update (Section 3.1, iteration steps 2-3) ------
     // Each found (f, v) adds G'^_{b'L-u} v e^{2 pi i f o_r / N} to buckets b' = b(u)-1..b(u)+1
     // of every round r.  Contributions accumulate in int64 fixed point (2^(fx-40) units,
-    // fx = exponent of the largest bucket of iteration 1) with integer atomics, so the sum
-    // does not depend on the order of the additions.  Rounds are processed in passes of
-    // `rc` rounds with `nco` warp-private copies of the accumulators (many entries share few
-    // buckets when B is small); per-entry invariants are computed once.
+    // fx = exponent of the largest bucket of iteration 1), so the sum does not depend on the
+    // order of the additions.  Gather form: the found entries (v, f and G'^ for their three
+    // buckets) are staged in shared memory in bucket order; per pass of kUpdRounds rounds the
+    // rotated values v e^{2 pi i f o_r / N} are computed once per entry, then each (bucket b',
+    // split) work item sums the entries of b'-1, b', b'+1 in registers; with several splits
+    // per bucket (B < block size) the partial sums are added in a fixed order.  For
+    // B > kGatherMaxB, or when the staged entries do not fit in shared memory, the entries
+    // scatter their contributions with integer atomics into warp-private accumulator copies
+    // instead (the same integer sums).
     if (!a.first && F0 > 0) {
         const int fx = s_fx;
         const float scale = ldexpf(1.f, 40 - fx);
         const float iscale = ldexpf(1.f, fx - 40);
-        const size_t budget = decode_smem(B) / sizeof(long long);  // int64 slots available
-        const int per_round = 2 * B;
-        int rc = (int)((size_t)R < budget / per_round ? (size_t)R : budget / per_round);
-        if (rc < 1) rc = 1;
-        const size_t ncmax = budget / ((size_t)rc * per_round);
-        int nco = (int)((size_t)(T >> 5) < ncmax ? (size_t)(T >> 5) : ncmax);
-        if (nco < 1) nco = 1;
-        long long* wacc = acc + (size_t)((tid >> 5) % nco) * rc * per_round;
-        for (int r0 = 0; r0 < R; r0 += rc) {
-            const int nr = min(rc, R - r0);
-            for (int i = tid; i < nco * rc * per_round; i += T) acc[i] = 0;
+        // shared memory: bucket offsets, then per staged entry v (float2), f, G'^ (3), and the
+        // rotated values c_r = v e^{2 pi i f o_r / N} of the current pass (kUpdRounds float2),
+        // then (several splits per bucket) the splits' partial sums
+        const int splits = B < T ? min(8, T / B) : 1;
+        const size_t off_v = ((size_t)4 * (2 * B + 1) + 7) & ~(size_t)7;
+        const size_t off_c = off_v + (size_t)8 * F0;
+        const size_t off_f = off_c + (size_t)8 * kUpdRounds * F0;
+        const size_t off_g = off_f + (size_t)4 * F0;
+        const size_t acc_off = (off_g + (size_t)12 * F0 + 15) & ~(size_t)15;
+        const size_t need = acc_off + (splits > 1 ? (size_t)16 * kUpdRounds * splits * B : 0);
+        if (B <= kGatherMaxB && need <= decode_smem(B)) {
+            int* cnt = (int*)smraw;          // B + 1: counts, then offsets of each bucket's entries
+            int* fillp = cnt + (B + 1);      // B: placement cursors
+            float2* ev = (float2*)(smraw + off_v);
+            float2* ec = (float2*)(smraw + off_c);
+            uint32_t* ef = (uint32_t*)(smraw + off_f);
+            float* eg = (float*)(smraw + off_g);
+            long long* part = (long long*)(smraw + acc_off);
+            for (int b = tid; b <= B; b += T) cnt[b] = 0;
             __syncthreads();
-            for (int i = tid; i < F0; i += T) {
-                const uint32_t f = (uint32_t)ff[i];
-                const double2 vd = fv[i];
-                const float2 v = make_float2((float)vd.x, (float)vd.y);
+            for (int e = tid; e < F0; e += T) {
+                const uint32_t u = (sigma * (uint32_t)ff[e]) & mask;
+                atomicAdd(&cnt[(((u + (L >> 1)) >> logL) & (uint32_t)(B - 1))], 1);
+            }
+            __syncthreads();
+            {
+                const int Eb = (B + T - 1) / T;
+                const int lo = min(B, tid * Eb), hi = min(B, lo + Eb);
+                int loc = 0;
+                for (int b = lo; b < hi; ++b) loc += cnt[b];
+                int tot;
+                int run = block_exscan(loc, s_ws, &tot);
+                for (int b = lo; b < hi; ++b) {
+                    const int c = cnt[b];
+                    cnt[b] = run;
+                    fillp[b] = run;
+                    run += c;
+                }
+                if (tid == 0) cnt[B] = tot;
+            }
+            __syncthreads();
+            for (int e = tid; e < F0; e += T) {
+                const uint32_t f = (uint32_t)ff[e];
+                const double2 vd = fv[e];
                 const uint32_t u = (sigma * f) & mask;
                 const int b0 = (int)(((u + (L >> 1)) >> logL) & (uint32_t)(B - 1));
                 float g3[3];
-                int bb[3];
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    bb[q] = (b0 + q - 1) & (B - 1);
-                    const int k = (int)((((uint32_t)bb[q] * L - u) + halfN) & mask) - (int)halfN;
+                    const int bb = (b0 + q - 1) & (B - 1);
+                    const int k = (int)((((uint32_t)bb * L - u) + halfN) & mask) - (int)halfN;
                     g3[q] = it->Ghat[k < 0 ? -k : k] * scale;
                 }
-                for (int rr = 0; rr < nr; ++rr) {
-                    const uint32_t o_r = (aoff + sigma * (uint32_t)it->tau[r0 + rr]) & mask;
-                    const float2 c = cmul(v, cis_2pi_frac((f * o_r) & mask, n));
-                    long long* ar = wacc + (size_t)rr * per_round;
+                const int pos = atomicAdd(&fillp[b0], 1);
+                ev[pos] = make_float2((float)vd.x, (float)vd.y);
+                ef[pos] = f;
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        atomicAdd((unsigned long long*)&ar[2 * bb[q]], (unsigned long long)__float2ll_rn(g3[q] * c.x));
-                        atomicAdd((unsigned long long*)&ar[2 * bb[q] + 1], (unsigned long long)__float2ll_rn(g3[q] * c.y));
+                for (int q = 0; q < 3; ++q) eg[3 * pos + q] = g3[q];
+            }
+            __syncthreads();
+            for (int r0 = 0; r0 < R; r0 += kUpdRounds) {
+                const int nr = min(kUpdRounds, R - r0);
+                for (int i = tid; i < F0 * kUpdRounds; i += T) {
+                    const int pos = i / kUpdRounds, rr = i - pos * kUpdRounds;
+                    if (rr < nr) {
+                        const uint32_t o_r = (aoff + sigma * (uint32_t)it->tau[r0 + rr]) & mask;
+                        ec[i] = cmul(ev[pos], cis_2pi_frac((ef[pos] * o_r) & mask, n));
                     }
                 }
-            }
-            __syncthreads();
-            for (int e = tid; e < nr * B; e += T) {
-                const int rr = e / B, b = e - rr * B;
-                long long sr = 0, si = 0;
-                for (int w = 0; w < nco; ++w) {
-                    const long long* aw = acc + ((size_t)w * rc + rr) * per_round;
-                    sr += aw[2 * b];
-                    si += aw[2 * b + 1];
+                __syncthreads();
+                for (int item = tid; item < B * splits; item += T) {
+                    const int bp = item % B, sp = item / B;
+                    long long ar[kUpdRounds], ai[kUpdRounds];
+#pragma unroll
+                    for (int rr = 0; rr < kUpdRounds; ++rr) ar[rr] = ai[rr] = 0;
+#pragma unroll
+                    for (int q = -1; q <= 1; ++q) {
+                        // entries of bucket bp + q reach bp with their G'^ at offset -q
+                        const int bb = (bp + q) & (B - 1);
+                        const int j1 = cnt[bb + 1];
+                        for (int j = cnt[bb] + sp; j < j1; j += splits) {
+                            const float g = eg[3 * j + 1 - q];
+#pragma unroll
+                            for (int rr = 0; rr < kUpdRounds; ++rr) {
+                                if (rr < nr) {
+                                    const float2 c = ec[j * kUpdRounds + rr];
+                                    ar[rr] += f2ll_rn(g * c.x);
+                                    ai[rr] += f2ll_rn(g * c.y);
+                                }
+                            }
+                        }
+                    }
+                    if (splits == 1) {
+#pragma unroll
+                        for (int rr = 0; rr < kUpdRounds; ++rr) {
+                            if (rr < nr) {
+                                float2* yp = &Y[(int64_t)(r0 + rr) * B + bp];
+                                float2 yv = *yp;
+                                yv.x -= ll2f_rn(ar[rr]) * iscale;
+                                yv.y -= ll2f_rn(ai[rr]) * iscale;
+                                *yp = yv;
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int rr = 0; rr < kUpdRounds; ++rr) {
+                            long long* pp = part + 2 * ((size_t)(sp * kUpdRounds + rr) * B + bp);
+                            pp[0] = ar[rr];
+                            pp[1] = ai[rr];
+                        }
+                    }
                 }
-                float2* yp = &Y[(int64_t)(r0 + rr) * B + b];
-                float2 yv = *yp;
-                yv.x -= __ll2float_rn(sr) * iscale;
-                yv.y -= __ll2float_rn(si) * iscale;
-                *yp = yv;
+                if (splits > 1) {
+                    __syncthreads();
+                    for (int e = tid; e < nr * B; e += T) {
+                        const int rr = e / B, b = e - rr * B;
+                        long long sr = 0, si = 0;
+                        for (int sp = 0; sp < splits; ++sp) {
+                            const long long* pp = part + 2 * ((size_t)(sp * kUpdRounds + rr) * B + b);
+                            sr += pp[0];
+                            si += pp[1];
+                        }
+                        float2* yp = &Y[(int64_t)(r0 + rr) * B + b];
+                        float2 yv = *yp;
+                        yv.x -= ll2f_rn(sr) * iscale;
+                        yv.y -= ll2f_rn(si) * iscale;
+                        *yp = yv;
+                    }
+                }
+                __syncthreads();
             }
-            __syncthreads();
+        } else {
+            const size_t budget = decode_smem(B) / sizeof(long long);  // int64 slots available
+            const int per_round = 2 * B;
+            int rc = (int)((size_t)R < budget / per_round ? (size_t)R : budget / per_round);
+            if (rc < 1) rc = 1;
+            const size_t ncmax = budget / ((size_t)rc * per_round);
+            int nco = (int)((size_t)(T >> 5) < ncmax ? (size_t)(T >> 5) : ncmax);
+            if (nco < 1) nco = 1;
+            long long* wacc = acc + (size_t)((tid >> 5) % nco) * rc * per_round;
+            for (int r0 = 0; r0 < R; r0 += rc) {
+                const int nr = min(rc, R - r0);
+                for (int i = tid; i < nco * rc * per_round; i += T) acc[i] = 0;
+                __syncthreads();
+                for (int i = tid; i < F0; i += T) {
+                    const uint32_t f = (uint32_t)ff[i];
+                    const double2 vd = fv[i];
+                    const float2 v = make_float2((float)vd.x, (float)vd.y);
+                    const uint32_t u = (sigma * f) & mask;
+                    const int b0 = (int)(((u + (L >> 1)) >> logL) & (uint32_t)(B - 1));
+                    float g3[3];
+                    int bb[3];
+    #pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        bb[q] = (b0 + q - 1) & (B - 1);
+                        const int k = (int)((((uint32_t)bb[q] * L - u) + halfN) & mask) - (int)halfN;
+                        g3[q] = it->Ghat[k < 0 ? -k : k] * scale;
+                    }
+                    for (int rr = 0; rr < nr; ++rr) {
+                        const uint32_t o_r = (aoff + sigma * (uint32_t)it->tau[r0 + rr]) & mask;
+                        const float2 c = cmul(v, cis_2pi_frac((f * o_r) & mask, n));
+                        long long* ar = wacc + (size_t)rr * per_round;
+    #pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            atomicAdd((unsigned long long*)&ar[2 * bb[q]], (unsigned long long)f2ll_rn(g3[q] * c.x));
+                            atomicAdd((unsigned long long*)&ar[2 * bb[q] + 1], (unsigned long long)f2ll_rn(g3[q] * c.y));
+                        }
+                    }
+                }
+                __syncthreads();
+                for (int e = tid; e < nr * B; e += T) {
+                    const int rr = e / B, b = e - rr * B;
+                    long long sr = 0, si = 0;
+                    for (int w = 0; w < nco; ++w) {
+                        const long long* aw = acc + ((size_t)w * rc + rr) * per_round;
+                        sr += aw[2 * b];
+                        si += aw[2 * b + 1];
+                    }
+                    float2* yp = &Y[(int64_t)(r0 + rr) * B + b];
+                    float2 yv = *yp;
+                    yv.x -= ll2f_rn(sr) * iscale;
+                    yv.y -= ll2f_rn(si) * iscale;
+                    *yp = yv;
+                }
+                __syncthreads();
+            }
         }
     }
 
