@@ -155,15 +155,22 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def fold_source_sha256():
+    """sha256 of the fold kernel's source: kernels.cu from its fold section header up to the
+    FFT section header."""
+    src = open(os.path.join(ROOT, "paper_2011_05698_gb300", "csrc", "kernels.cu")).read()
+    a = src.index("// ----------------------------------------------------------------- fold")
+    b = src.index("// ----------------------------------------------------------------- FFT")
+    return hashlib.sha256(src[a:b].encode()).hexdigest()
+
+
 def fold_traffic_record():
-    """DRAM bytes per fold launch from the committed ncu summary, if the kernel source is
-    unchanged since the capture (else None)."""
+    """DRAM bytes per fold launch from the committed ncu summary, if the fold kernel's source
+    is unchanged since the capture (else None)."""
     path = os.path.join(ROOT, "profiles", "fold_traffic.json")
-    src = os.path.join(ROOT, "paper_2011_05698_gb300", "csrc", "kernels.cu")
     try:
         rec = json.load(open(path))
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if rec.get("kernels_cu_sha256") != h:
+        if rec.get("fold_source_sha256") != fold_source_sha256():
             return None
         return rec
     except (OSError, ValueError):
