@@ -219,11 +219,7 @@ def uneven_form(s4, args, dev, stream, dist):
         bp.execute(xs, out=out, ptrs=ptrs)
 
     steps = max(3, min(args.steps, 20))
-    el = timed(step, steps, args.warmup, stream, dist)
-    if dist is not None:
-        t = torch.tensor([el], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
+    el = max_over_ranks(timed(step, steps, args.warmup, stream, dist), dist, dev)
     world = dist.get_world_size() if dist is not None else 1
     info = dict(bp.info)
     bp.close()
@@ -362,6 +358,36 @@ def sweep_form(s4, args, dev, stream):
             "rows": rows}
 
 
+# --------------------------------------------------------------------------- ranks
+def init_ranks(backend="nccl"):
+    """(rank, world, local_rank, dist) from the torchrun environment; dist is the initialised
+    torch.distributed module when world > 1, else None."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group(backend)
+        dist = tdist
+    return rank, world, local, dist
+
+
+def max_over_ranks(x, dist, device):
+    """The maximum of x over all ranks (x itself on one rank)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_seed0(rank):
+    """First signal seed of a rank's batch: replicas transform disjoint synthetic batches."""
+    return 1_000_000 * (rank + 1)
+
+
 def timed(fn, steps, warmup, stream, dist=None):
     import torch
     for _ in range(warmup):
@@ -407,7 +433,6 @@ def main():
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         reference_arm(args, rank, world)
         return
@@ -419,11 +444,7 @@ def main():
         pool = make_pool(cpu_workers)
 
     import torch
-    dist = None
-    if world > 1:
-        import torch.distributed as tdist
-        tdist.init_process_group("nccl")
-        dist = tdist
+    rank, world, local, dist = init_ranks("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     from paper_2011_05698_gb300 import build
@@ -455,7 +476,7 @@ def main():
     S = args.batch
     plan = s4.Plan(N_DEF, K_DEF, L_DEF, Q_DEF, seed=1234, max_batch=S, profile=True,
                    precision=args.precision)
-    xs = device_batch(N_DEF, K_DEF, S, 1_000_000 * (rank + 1), args.snr, dev)
+    xs = device_batch(N_DEF, K_DEF, S, rank_seed0(rank), args.snr, dev)
     out = plan._outputs(S)
     stream = torch.cuda.current_stream(dev)
 
@@ -469,10 +490,7 @@ def main():
     with ClockSampler(local) as clk:
         el = timed(step, args.steps, 0, stream, dist)
     prof = plan.profile(reset=True)
-    if dist is not None:
-        t = torch.tensor([el], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
+    el = max_over_ranks(el, dist, dev)
     value = S * args.steps * world / el
     ms_per_step = 1e3 * el / args.steps
 
@@ -554,11 +572,7 @@ def main():
         stream.wait_stream(copy_stream)
         e1.record(stream)
         torch.cuda.synchronize()
-        ee = e0.elapsed_time(e1) / 1e3
-        if dist is not None:
-            t = torch.tensor([ee], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ee = float(t.item())
+        ee = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist, dev)
         h2d = Se * N_DEF * 8
         d2h = sum(t.numel() * t.element_size() for t in oute)
         e2e = {"value": Se * esteps * world / ee, "unit": "transforms/s", "h2d_bytes_per_step": h2d,
@@ -575,7 +589,8 @@ def main():
         plan_f = s4.Plan(N_DEF, K_DEF, L_DEF, Q_DEF, seed=1234, max_batch=S, precision="fp32")
         outf = plan_f._outputs(S)
         steps_f = max(3, min(args.steps, 50))
-        ef = timed(lambda: plan_f.execute_batched(xs, outf), steps_f, args.warmup, stream, dist)
+        ef = max_over_ranks(timed(lambda: plan_f.execute_batched(xs, outf), steps_f, args.warmup, stream, dist),
+                            dist, dev)
         fp32_form = {"value": S * steps_f * world / ef, "unit": "transforms/s", "steps": steps_f,
                      "form": "batched sfft4_execute_batched, FP32 radix-2 DFT"}
         plan_f.close()
