@@ -243,6 +243,57 @@ def uneven_form(s4, args, dev, stream, dist):
             "kernel_ms_one_execute": {k: prof[k + "_ms"] for k in ("fold", "fft", "decode", "finalize")}}
 
 
+def phase_errors(Y, freqs, sigma, N, B, taus):
+    """Phase errors |dPhi| (radians) of the levels s = 1..S for every tone alone in its bucket
+    neighbourhood: dPhi = wrap(arg(y_s[b] conj(y_0[b])) - 2 pi (u tau_s mod N) / N), u = sigma f
+    mod N, b = bucket of u (the location's phase measurement, Section 3.2, Eq. 16-19)."""
+    import numpy as np
+    L = N // B
+    u = (sigma * freqs.astype(np.uint64)) & np.uint64(N - 1)
+    b = (((u + np.uint64(L // 2)) // np.uint64(L)) % np.uint64(B)).astype(np.int64)
+    occ = np.bincount(b, minlength=B)
+    near = occ + np.roll(occ, 1) + np.roll(occ, -1)
+    alone = near[b] == 1
+    out = []
+    for s_ in range(1, len(taus)):
+        ideal = ((u[alone] * np.uint64(taus[s_])) & np.uint64(N - 1)).astype(np.float64) / N
+        meas = np.angle(Y[s_, b[alone]] * np.conj(Y[0, b[alone]])) / (2 * np.pi)
+        d = (meas - ideal + 0.5) % 1.0 - 0.5
+        out.append(np.abs(d) * 2 * np.pi)
+    return np.concatenate(out) if out else np.zeros(0)
+
+
+def phase_error_form(s4, args, dev):
+    """Monte Carlo of the location's phase error (Section 3.2, Fig. 5): K = 50 tones, SNR in
+    {-20, -10, 0, 20, 40, 60, 120} dB, bucket lengths L = N / B from 128 to 8192; iteration-1
+    bucket arrays of the library (sfft4_bucketize), 64 signals per point.  Reports quantiles of
+    |dPhi| and the bounds they imply: l <= pi / max dPhi (Eq. 18), q >= max dPhi l / pi (Eq. 19),
+    with max dPhi the 0.99 quantile."""
+    import numpy as np
+    from synth.signals import device_signal
+    K, trials = 50, 64
+    rows = []
+    for N, B in ((2**13, 64), (2**17, 64), (2**20, 512), (2**22, 512)):
+        p = s4.Plan(N, K, 16, 1.0, seed=99, B1=B)
+        it = p.iter_info(1)
+        for snr in (-20.0, -10.0, 0.0, 20.0, 40.0, 60.0, 120.0):
+            errs = []
+            for t in range(trials):
+                x, f, _ = device_signal(N, K, 40_000 + t, snr, dev)
+                Y = p.bucketize(x, 1, signal=t).cpu().numpy().astype(np.complex128)
+                sigma, _ = p.permutation(1, signal=t)
+                errs.append(phase_errors(Y, f, np.uint64(sigma), N, B, it["tau"]))
+            e = np.concatenate(errs)
+            q99 = float(np.quantile(e, 0.99))
+            rows.append({"N": N, "B": B, "L": N // B, "snr_db": snr, "samples": int(e.size),
+                         "median_rad": float(np.median(e)), "q99_rad": q99,
+                         "log10_q99": float(np.log10(max(q99, 1e-300))),
+                         "l_upper_bound": float(np.pi / q99) if q99 > 0 else None,
+                         "q_lower_bound_at_l16": float(q99 * 16 / np.pi)})
+        p.close()
+    return {"form": "phase_error", "K": K, "trials": trials, "data": "synthetic", "rows": rows}
+
+
 def configs_form(s4, args, dev, stream):
     """The small single-signal configurations over 10 seeds each: N = 2^14, K = 16 (l = 4,
     q = 0.5, B1 = 64, noiseless) and N = 2^20, K = 100 (l = 16, q = 1, B1 = 128, 20 dB), plus
@@ -422,7 +473,7 @@ def main():
     ap.add_argument("--plain-signals", type=int, default=16)
     ap.add_argument("--uneven-signals", type=int, default=512)
     ap.add_argument("--no-fp32-form", action="store_true")
-    ap.add_argument("--form", default="all", choices=["all", "uneven", "sweep", "configs"],
+    ap.add_argument("--form", default="all", choices=["all", "uneven", "sweep", "configs", "phase_error"],
                     help="uneven: time only the uneven-batch form; sweep: the large-N SNR x (l, q) "
                          "sweep (N = 2^26, K = 4000, 10 seeds)")
     ap.add_argument("--sweep-seeds", type=int, default=10)
@@ -450,6 +501,13 @@ def main():
     from paper_2011_05698_gb300 import build
     build.build()
     import paper_2011_05698_gb300 as s4
+
+    if args.form == "phase_error":
+        if rank == 0:
+            print(json.dumps(phase_error_form(s4, args, dev)), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
 
     if args.form == "configs":
         if rank == 0:
@@ -616,7 +674,7 @@ def main():
         uneven = uneven_form(s4, args, dev, stream, dist)
 
     # plain form: one signal per execute call, FP32 DFT
-    plain = None
+    plain = plain_graph = None
     if args.plain_signals > 0:
         plan_p = s4.Plan(N_DEF, K_DEF, L_DEF, Q_DEF, seed=1234, precision="fp32")
         outp = plan_p._outputs(1)
@@ -629,6 +687,21 @@ def main():
         pe = timed(step_p, 2, 1, stream, None)
         plain = {"value": ns * 2 / pe, "unit": "transforms/s", "form": "single-signal sfft4_execute, FP32 DFT"}
         plan_p.close()
+        # the same with the execute captured once as a CUDA graph and replayed (same buffers)
+        plan_g = s4.Plan(N_DEF, K_DEF, L_DEF, Q_DEF, seed=1234, precision="fp32", graph=True)
+        outg = plan_g._outputs(1)
+        xg = torch.empty(N_DEF, dtype=torch.complex64, device=dev)
+
+        def step_g():
+            for i in range(ns):
+                xg.copy_(xs[i])
+                plan_g.execute(xg, outg)
+
+        pg = timed(step_g, 2, 1, stream, None)
+        plain_graph = {"value": ns * 2 / pg, "unit": "transforms/s",
+                       "form": "single-signal sfft4_execute replayed as one CUDA graph per call, FP32 DFT "
+                               "(includes a 32 MB device copy of each signal into the captured buffer)"}
+        plan_g.close()
 
     cpu = None
     if pool is not None:
@@ -653,7 +726,7 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": plan.info["kernels_per_execute"] * args.steps,
                 "clocks": clk.summary(), "forms": {"batched": {"value": value, "precision": args.precision},
-                                                   "batched_fp32": fp32_form, "plain_fp32": plain,
+                                                   "batched_fp32": fp32_form, "plain_fp32": plain, "plain_fp32_graph": plain_graph,
                                                    "uneven_batch": uneven, "dense_fft_context": dense}}
         print(json.dumps(line), flush=True)
     plan.close()

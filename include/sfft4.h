@@ -195,6 +195,17 @@ typedef struct {
 /* Static plan summary.  Errors: SFFT4_EINVAL on NULL arguments. */
 SFFT4_API int sfft4_get_plan_info(sfft4_plan_t plan, sfft4_plan_info* info);
 
+/*
+ * sfft4_get_permutation -- the random spectral permutation of iteration m (1-based) of
+ * signal `signal` (Section 2.2, Eq. 7-8): *sigma (odd) and *a in [0, N), drawn by
+ * Philox4x64-10 with counter (signal, m, 0, 0) and key (seed, 0) as the kernels draw them.
+ * The gather of round s reads x[(sigma t + a + sigma tau_s) mod N]; frequency f moves to
+ * u = sigma f mod N.  Host-only; no device work.
+ * Errors: SFFT4_EINVAL (NULL pointers, m out of range, signal < 0), SFFT4_ESTATE (plan from
+ * sfft4_plan_batched).
+ */
+SFFT4_API int sfft4_get_permutation(sfft4_plan_t plan, int64_t signal, int32_t m, uint64_t* sigma, uint64_t* a);
+
 #define SFFT4_MAX_ROUNDS 64
 typedef struct {
     int32_t B;                 /* buckets B_m */

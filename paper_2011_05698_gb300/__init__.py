@@ -119,6 +119,13 @@ class Plan:
                 "Lbar": list(it.Lbar[:S]), "tau": list(it.tau[:S + 1]), "H": list(it.H[:S]),
                 "unique_samples": it.unique_samples}
 
+    def permutation(self, m, signal=0):
+        """(sigma, a) of iteration m for Philox signal index `signal` (f moves to sigma f mod N)."""
+        s, a = ctypes.c_uint64(), ctypes.c_uint64()
+        check(_lib.load().sfft4_get_permutation(self._h, signal, m, ctypes.byref(s), ctypes.byref(a)),
+              "sfft4_get_permutation")
+        return s.value, a.value
+
     def window(self, B):
         """(G, Ghat) host float32 arrays of bucket count B."""
         import numpy as np

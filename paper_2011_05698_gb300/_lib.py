@@ -75,6 +75,8 @@ SIGNATURES = [
     ("sfft4_get_batch_info", ctypes.c_int, [_P, ctypes.POINTER(BatchInfo)]),
     ("sfft4_get_plan_info", ctypes.c_int, [_P, ctypes.POINTER(PlanInfo)]),
     ("sfft4_get_iter_info", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(IterInfo)]),
+    ("sfft4_get_permutation", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64),
+                                             ctypes.POINTER(ctypes.c_uint64)]),
     ("sfft4_get_window", ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
     ("sfft4_bucketize", ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P]),
     ("sfft4_trace_get", ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, _P, _P, _P, _P]),

@@ -476,6 +476,13 @@ int sfft4_get_plan_info(sfft4_plan_t p, sfft4_plan_info* info) {
     return SFFT4_OK;
 }
 
+int sfft4_get_permutation(sfft4_plan_t p, int64_t signal, int32_t m, uint64_t* sigma, uint64_t* a) {
+    if (p && p->grp) return SFFT4_ESTATE;
+    if (!p || !sigma || !a || signal < 0 || m < 1 || m > (int32_t)p->iters.size()) return SFFT4_EINVAL;
+    permutation_draw(p->seed, (uint64_t)signal, (uint64_t)p->iters[m - 1].d.m, (uint64_t)p->N, sigma, a);
+    return SFFT4_OK;
+}
+
 int sfft4_get_iter_info(sfft4_plan_t p, int32_t m, sfft4_iter_info* info) {
     if (p && p->grp) return SFFT4_ESTATE;
     if (!p || !info || m < 1 || m > (int32_t)p->iters.size()) return SFFT4_EINVAL;
