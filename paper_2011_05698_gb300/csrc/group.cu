@@ -1,12 +1,14 @@
 // Batched sFFT4.0 over signals of different sizes N_i and sparsities K_i in one pass of
 // table-driven kernels.
 //
-// Signals with equal (N, K) share one static schedule ("class", Section 3.1); window tables
-// are shared by (N, B).  Execution is level-synchronous: level m runs iteration m of every
-// signal whose schedule has one.  Each level is a handful of launches whose CTAs take their
-// work from device tables built here: fold tiles (signal, fold group, residue slice), DFT
-// columns grouped by bucket count, decode jobs grouped by round count.  A whole execute can be
-// captured as one CUDA graph (opts.graph).
+// Signals with equal (N, K, B1) share one static schedule ("class", Section 3.1); window
+// tables are shared by (N, B).  Level m of an execute is iteration m of every signal whose
+// schedule has one: a handful of launches whose CTAs take their work from device tables built
+// here (fold tiles (signal, fold group, residue slice), DFT columns grouped by bucket count,
+// decode jobs grouped by round count).  The bucketization of all levels runs on the caller's
+// stream and the decode chain on a second stream, level m as soon as its bucket arrays exist,
+// since the bucketization never reads the found sets.  A whole execute can be captured as one
+// CUDA graph (opts.graph).
 #include <stdio.h>
 #include <string.h>
 
@@ -105,6 +107,8 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 void destroy_group(Group* g) { free_group(g); }
 
+size_t group_levels(const Group* g) { return g->levels.size(); }
+
 int build_group_plan(sfft4_plan_s* p, int nsig, const int64_t* Ns, const int64_t* Ks, const int32_t* B1s,
                      int32_t l, double q, uint64_t seed, const sfft4_opts* opts) {
     Group* g = new (std::nothrow) Group();
@@ -161,7 +165,7 @@ int build_group_plan(sfft4_plan_s* p, int nsig, const int64_t* Ns, const int64_t
         const sfft4_plan_s* c = g->cls[g->slot_cls[i]];
         const size_t rb = (size_t)c->R_max * c->B_max * sizeof(float2);
         so[i].z = take(rb);
-        so[i].y = take(rb);
+        so[i].y = take((size_t)c->ytot * sizeof(float2));  // every iteration's bucket arrays
         so[i].u = (p->o.precision == SFFT4_BF16X3) ? take(rb) : 0;
         so[i].ff = take((size_t)c->Fcap * 4);
         so[i].fv = take((size_t)c->Fcap * 16);
@@ -229,7 +233,7 @@ int build_group_plan(sfft4_plan_s* p, int nsig, const int64_t* Ns, const int64_t
                 for (int r = 0; r < ih.d.R; ++r) {
                     zc.push_back((const float2*)(A + so[i].z) + (int64_t)r * ih.d.B);
                     uc.push_back(so[i].u ? (float2*)(A + so[i].u) + (int64_t)r * ih.d.B : nullptr);
-                    yc.push_back((float2*)(A + so[i].y) + (int64_t)r * ih.d.B);
+                    yc.push_back((float2*)(A + so[i].y) + c->yoff[mi] + (int64_t)r * ih.d.B);
                 }
             }
             d.n = (int)((int64_t)zc.size() - d.off);
@@ -246,7 +250,7 @@ int build_group_plan(sfft4_plan_s* p, int nsig, const int64_t* Ns, const int64_t
                 if (cl != rcl) continue;
                 DecodeArgs a = make_decode_args(c, mi);
                 a.signal0 = i;
-                a.y = (float2*)(A + so[i].y);
+                a.y = (float2*)(A + so[i].y) + c->yoff[mi];
                 a.F = g->F + i;
                 a.ff = (int32_t*)(A + so[i].ff);
                 a.fv = (double2*)(A + so[i].fv);
@@ -303,10 +307,17 @@ struct GroupRun {
 int group_body(sfft4_plan_s* p, const void* ctx, cudaStream_t st) {
     const GroupRun& r = *(const GroupRun*)ctx;
     Group* g = p->grp;
+    // bucketization of every level on the caller's stream, the decode chain on the plan's
+    // decode stream (level m after its bucket arrays exist): the bucketization never reads
+    // the found sets, so later levels' folds overlap earlier levels' decodes
+    cudaStream_t ds = p->dstream;
     int rc = check_cuda(cudaMemsetAsync(g->F, 0, (size_t)g->nsig * sizeof(int32_t), st));
     if (!rc) rc = check_cuda(cudaMemsetAsync(g->hkeys, 0xff, g->hkeys_count * sizeof(int32_t), st));
+    if (!rc) rc = check_cuda(cudaEventRecord(p->ev[0], st));
+    if (!rc) rc = check_cuda(cudaStreamWaitEvent(ds, p->ev[0], 0));
     if (rc) return rc;
-    for (const GroupLevel& L : g->levels) {
+    for (size_t li = 0; li < g->levels.size(); ++li) {
+        const GroupLevel& L = g->levels[li];
         for (const auto& f : L.folds) {
             cudaEvent_t ev = nullptr;
             rc = prof_begin(p, st, &ev);
@@ -333,18 +344,23 @@ int group_body(sfft4_plan_s* p, const void* ctx, cudaStream_t st) {
                 if (rc) return rc;
             }
         }
+        rc = check_cuda(cudaEventRecord(p->ev[1 + li], st));
+        if (!rc) rc = check_cuda(cudaStreamWaitEvent(ds, p->ev[1 + li], 0));
+        if (rc) return rc;
         for (const auto& d : L.decs) {
             cudaEvent_t ev = nullptr;
-            rc = prof_begin(p, st, &ev);
-            if (!rc) rc = launch_decode_multi(d.rclass, g->dec_jobs, g->dec_list + d.off, d.n, d.smem, st);
-            if (!rc) rc = prof_end(p, st, ev, kProfDecode, 0);
+            rc = prof_begin(p, ds, &ev);
+            if (!rc) rc = launch_decode_multi(d.rclass, g->dec_jobs, g->dec_list + d.off, d.n, d.smem, ds);
+            if (!rc) rc = prof_end(p, ds, ev, kProfDecode, 0);
             if (rc) return rc;
         }
     }
     cudaEvent_t ev = nullptr;
-    rc = prof_begin(p, st, &ev);
-    if (!rc) rc = launch_finalize_multi(g->fin_jobs, g->nsig, g->Kmax, r.idx, r.val, r.nfound, r.votes, st);
-    if (!rc) rc = prof_end(p, st, ev, kProfFinalize, 0);
+    rc = prof_begin(p, ds, &ev);
+    if (!rc) rc = launch_finalize_multi(g->fin_jobs, g->nsig, g->Kmax, r.idx, r.val, r.nfound, r.votes, ds);
+    if (!rc) rc = prof_end(p, ds, ev, kProfFinalize, 0);
+    if (!rc) rc = check_cuda(cudaEventRecord(p->ev[1 + g->levels.size()], ds));
+    if (!rc) rc = check_cuda(cudaStreamWaitEvent(st, p->ev[1 + g->levels.size()], 0));
     return rc;
 }
 }  // namespace

@@ -1237,8 +1237,8 @@ DecodeArgs make_decode_args(const sfft4_plan_s* p, int mi) {
     a.mag_tol = (float)p->o.mag_tol;
     a.sig_floor = (float)p->o.sig_floor;
     a.it = p->iters_dev + mi;
-    a.y = p->y;
-    a.y_stride = (int64_t)p->R_max * p->B_max;
+    a.y = p->y + p->yoff[mi];
+    a.y_stride = p->ytot;
     a.F = p->F;
     a.ff = p->ff;
     a.fv = p->fv;
@@ -1456,32 +1456,45 @@ int run_body(sfft4_plan_s* p, const void* ctx, cudaStream_t st) {
     const int nsig = r.nsig;
     const float2* x = r.x;
     const int64_t x_stride = r.x_stride;
+    const size_t ni = p->iters.size();
+    // Bucketization of every iteration on the caller's stream; the decode chain on the plan's
+    // decode stream, iteration m after its bucket arrays exist (ev[1 + m]) and after decode
+    // m - 1 (stream order).  The bucketization never reads the found set.
+    cudaStream_t ds = p->dstream;
     int rc = launch_reset(p, nsig, st);
+    if (!rc) rc = check_cuda(cudaEventRecord(p->ev[0], st));
+    if (!rc) rc = check_cuda(cudaStreamWaitEvent(ds, p->ev[0], 0));
     if (rc) return rc;
     const int64_t rb = (int64_t)p->R_max * p->B_max;
-    for (size_t mi = 0; mi < p->iters.size(); ++mi) {
-        rc = launch_bucketize(p, (int)mi, nsig, x, x_stride, 0, p->y, rb, st);
+    for (size_t mi = 0; mi < ni; ++mi) {
+        float2* ym = p->y + p->yoff[mi];
+        rc = launch_bucketize(p, (int)mi, nsig, x, x_stride, 0, ym, p->ytot, st);
+        if (!rc) rc = check_cuda(cudaEventRecord(p->ev[1 + mi], st));
+        if (!rc) rc = check_cuda(cudaStreamWaitEvent(ds, p->ev[1 + mi], 0));
         if (rc) return rc;
         const IterDev& d = p->iters[mi].d;
         if (p->o.trace) {
-            rc = check_cuda(cudaMemcpyAsync(p->trace_y + mi * rb, p->y, (size_t)d.R * d.B * sizeof(float2),
-                                            cudaMemcpyDeviceToDevice, st));
+            rc = check_cuda(cudaMemcpyAsync(p->trace_y + mi * rb, ym, (size_t)d.R * d.B * sizeof(float2),
+                                            cudaMemcpyDeviceToDevice, ds));
             if (rc) return rc;
         }
-        rc = launch_decode(p, (int)mi, nsig, st);
+        rc = launch_decode(p, (int)mi, nsig, ds);
         if (rc) return rc;
         if (p->o.trace) {
-            rc = check_cuda(cudaMemcpyAsync(p->trace_F + mi, p->F, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+            rc = check_cuda(cudaMemcpyAsync(p->trace_F + mi, p->F, sizeof(int32_t), cudaMemcpyDeviceToDevice, ds));
             if (!rc) rc = check_cuda(cudaMemcpyAsync(p->trace_ff + mi * p->Fcap, p->ff, p->Fcap * sizeof(int32_t),
-                                                     cudaMemcpyDeviceToDevice, st));
+                                                     cudaMemcpyDeviceToDevice, ds));
             if (!rc) rc = check_cuda(cudaMemcpyAsync(p->trace_fv + mi * p->Fcap, p->fv, p->Fcap * sizeof(double2),
-                                                     cudaMemcpyDeviceToDevice, st));
+                                                     cudaMemcpyDeviceToDevice, ds));
             if (!rc) rc = check_cuda(cudaMemcpyAsync(p->trace_votes + mi * p->Fcap, p->fvotes, p->Fcap,
-                                                     cudaMemcpyDeviceToDevice, st));
+                                                     cudaMemcpyDeviceToDevice, ds));
             if (rc) return rc;
         }
     }
-    return launch_finalize(p, nsig, r.idx, r.val, r.nfound, r.votes, st);
+    rc = launch_finalize(p, nsig, r.idx, r.val, r.nfound, r.votes, ds);
+    if (!rc) rc = check_cuda(cudaEventRecord(p->ev[1 + ni], ds));
+    if (!rc) rc = check_cuda(cudaStreamWaitEvent(st, p->ev[1 + ni], 0));
+    return rc;
 }
 
 int run(sfft4_plan_s* p, int nsig, const float2* x, int64_t x_stride, int64_t* idx,

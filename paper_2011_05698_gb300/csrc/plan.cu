@@ -131,6 +131,9 @@ void free_plan(sfft4_plan_s* p) {
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->gstream) cudaStreamDestroy(p->gstream);
+    for (cudaEvent_t e : p->ev)
+        if (e) cudaEventDestroy(e);
+    if (p->dstream) cudaStreamDestroy(p->dstream);
     sfft4::destroy_group(p->grp);
     delete p;
 }
@@ -314,6 +317,12 @@ int plan_schedule(sfft4_plan_s* p) {
         p->iters.push_back(ih);
     }
     p->Hlog = ilog2(2 * p->Fcap + 2);
+    p->yoff.clear();
+    p->ytot = 0;
+    for (auto& ih : p->iters) {
+        p->yoff.push_back(p->ytot);
+        p->ytot += (int64_t)ih.d.R * ih.d.B;
+    }
     return SFFT4_OK;
 }
 
@@ -391,7 +400,10 @@ int sfft4_plan(sfft4_plan_t* out, int64_t N, int64_t K, int32_t l, double q, uin
     size_t mb = (size_t)o.max_batch;
     size_t rb = (size_t)p->R_max * p->B_max;
     CK(cudaMalloc(&p->z, mb * rb * sizeof(float2)));
-    CK(cudaMalloc(&p->y, mb * rb * sizeof(float2)));
+    CK(cudaMalloc(&p->y, mb * (size_t)p->ytot * sizeof(float2)));
+    CK(cudaStreamCreateWithFlags(&p->dstream, cudaStreamNonBlocking));
+    p->ev.assign(ni + 2, nullptr);
+    for (auto& e : p->ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     CK(cudaMalloc(&p->F, mb * sizeof(int32_t)));
     CK(cudaMalloc(&p->status, sizeof(int32_t)));
     CK(cudaMemset(p->status, 0, sizeof(int32_t)));
@@ -445,6 +457,9 @@ int sfft4_plan_batched(sfft4_plan_t* out, int32_t nsig, const int64_t* N, const 
     CK(cudaMemset(p->status, 0, sizeof(int32_t)));
     int rc = build_group_plan(p, nsig, N, K, B1, l, q, seed, opts);
     if (rc) { free_plan(p); return rc; }
+    CK(cudaStreamCreateWithFlags(&p->dstream, cudaStreamNonBlocking));
+    p->ev.assign(group_levels(p->grp) + 2, nullptr);
+    for (auto& e : p->ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     CK(cudaDeviceSynchronize());
     *out = p;
     return SFFT4_OK;

@@ -194,7 +194,9 @@ struct sfft4_plan_s {
     int64_t samples = 0;        // distinct samples per transform
     // workspace for o.max_batch signals
     float2* z = nullptr;        // [sig][R_max][B_max] folded, before the DFT
-    float2* y = nullptr;        // [sig][R_max][B_max] bucket arrays
+    float2* y = nullptr;        // [sig][ytot] bucket arrays of every iteration (iteration m at yoff[m])
+    std::vector<int64_t> yoff;  // offset of iteration m's R_m x B_m arrays within a signal's block
+    int64_t ytot = 0;           // sum over iterations of R_m B_m
     int32_t* F = nullptr;       // [sig] found count
     int32_t* ff = nullptr;      // [sig][Fcap] frequency
     double2* fv = nullptr;      // [sig][Fcap] value
@@ -217,6 +219,11 @@ struct sfft4_plan_s {
     sfft4::Group* grp = nullptr;  // set for plans from sfft4_plan_batched
     // CUDA graph of the last captured execute (opts.graph), keyed on its buffers
     cudaStream_t gstream = nullptr;
+    // the decode chain runs on its own stream, overlapping the bucketization of later
+    // iterations (which does not depend on it); ev[0] forks, ev[1 + m] marks iteration m's
+    // bucket arrays, ev.back() joins
+    cudaStream_t dstream = nullptr;
+    std::vector<cudaEvent_t> ev;
     cudaGraphExec_t gexec = nullptr;
     uint64_t gkey[8] = {};
     // profiling (opts.profile): event pairs recorded around launches, by kind
@@ -264,6 +271,7 @@ int graph_run(sfft4_plan_s* p, const uint64_t key[8], cudaStream_t st, int (*bod
 int build_group_plan(sfft4_plan_s* p, int nsig, const int64_t* N, const int64_t* K, const int32_t* B1, int32_t l,
                      double q, uint64_t seed, const sfft4_opts* opts);
 void destroy_group(Group* g);
+size_t group_levels(const Group* g);
 // Implemented in plan.cu.
 int plan_options(int64_t N, int64_t K, int32_t l, double q, const sfft4_opts* opts, sfft4_opts* out,
                  int* qn_out);
