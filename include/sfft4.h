@@ -42,7 +42,9 @@ extern "C" {
 
 /* ----------------------------------------------------------------- precision ------ */
 #define SFFT4_FP32 0        /* window, fold and B-point DFT in FP32 (CUDA cores)         */
-#define SFFT4_BF16X3 1      /* B-point DFT as a BF16x3 split-precision complex GEMM on   */
+#define SFFT4_BF16X3 1
+#define SFFT4_LOC_MULTISCALE 0
+#define SFFT4_LOC_TWO_ROUND 1      /* B-point DFT as a BF16x3 split-precision complex GEMM on   */
                             /* the tensor cores (tcgen05), FP32 accumulation             */
 
 typedef struct sfft4_plan_s* sfft4_plan_t;   /* opaque, library-owned */
@@ -81,6 +83,11 @@ typedef struct {
                                 launch).  Ignored when profile or trace is set.  The graph
                                 holds the buffer addresses: the caller keeps them valid
                                 while the plan may replay it                              */
+    int32_t location;        /* SFFT4_LOC_MULTISCALE (default; Section 3.2) or
+                                SFFT4_LOC_TWO_ROUND (sFFT3.0-style: rounds tau = 0 and 1, the
+                                phase of yhat_1 / yhat_0 is u / N; exactly sparse signals with
+                                few collisions; default B1 pow2ceil(8K); N <= 2^20, where FP32
+                                bucket arrays resolve its 1/(8N)-turn vote window)          */
 } sfft4_opts;
 
 /* Fills *opts with the defaults above.  Returns SFFT4_EINVAL if opts is NULL. */

@@ -107,6 +107,7 @@ class Plan:
     sig_floor: float       # candidate floor, relative to max |yhat_0|^2 of iteration 1
     mag_tol: float         # |yhat_s|^2 consistency tolerance of a vote (Eq. 14-15)
     iters: list = field(default_factory=list)
+    location: str = "multiscale"   # or "two_round" (sFFT3.0: rounds tau = 0, 1)
 
 
 def schedule(K, B1, max_iters=64):
@@ -130,9 +131,16 @@ def schedule(K, B1, max_iters=64):
     return out
 
 
-def make_iteration(m, N, n, B, l, qn, delta):
+def make_iteration(m, N, n, B, l, qn, delta, location="multiscale"):
     L = N // B
     h, _ = window_halfwidth(N, B, delta)
+    if location == "two_round":
+        # sFFT3.0 location in the same iterative framework (Section 3.1: R_m = 2): rounds
+        # tau = 0 and 1, so the phase of yhat_1 / yhat_0 is u / N itself; the 2L integers of
+        # the search region compete as a final level with spacing 1 / N.  A lone tone's phase
+        # sits on an integer up to rounding, so the vote takes 1/8 of the spacing (half of it
+        # would accept every phase, i.e. every mixture of colliding tones)
+        return Iteration(m=m, B=B, L=L, h=h, Lbar=[2 * L], tau=[0, 1], H=[(1 << (32 - n)) // 8])
     # The search region of bucket b is [bL - L, bL + L): the pass band plus both halves
     # of the transition band (L/2 < |k| < L) where the (L/N, L/2N) window still leaks.
     Lbar = levels(2 * L, l, qn)
@@ -159,7 +167,7 @@ def make_iteration(m, N, n, B, l, qn, delta):
 
 
 def make_plan(N, K, l, q, seed, B1=0, delta=1e-8, select_factor=2.0, min_votes=0,
-              sig_floor=1e-10, mag_tol=0.5, max_iters=64):
+              sig_floor=1e-10, mag_tol=0.5, max_iters=64, location="multiscale"):
     """Validate and build the static plan (same checks as the library's sfft4_plan)."""
     if N < 256 or N & (N - 1) or N > (1 << 30):
         raise ValueError("N must be a power of two in [2^8, 2^30]")
@@ -171,8 +179,15 @@ def make_plan(N, K, l, q, seed, B1=0, delta=1e-8, select_factor=2.0, min_votes=0
         raise ValueError("need 2 <= l <= 32, q >= 0 and l > q + 1")
     if not (0.0 < delta < 0.5):
         raise ValueError("need 0 < delta < 1/2")
+    if location not in ("multiscale", "two_round"):
+        raise ValueError("location must be 'multiscale' or 'two_round'")
+    if location == "two_round" and N > (1 << 20):
+        # the library's FP32 bucket arrays resolve the 1/(8N)-turn vote window up to 2^20
+        raise ValueError("two-round location needs N <= 2^20")
+
     if B1 == 0:
-        B1 = max(B_MIN, min(4096, N // 64, pow2ceil(2 * K)))
+        # two-round location tolerates few collisions: default 8 K buckets instead of 2 K
+        B1 = max(B_MIN, min(4096, N // 64, pow2ceil((8 if location == "two_round" else 2) * K)))
         # reading R14: halve the default until the window of B1 buckets fits in N/2
         while B1 > B_MIN and 2 * window_halfwidth(N, B1, delta)[0] + 1 > N // 2:
             B1 //= 2
@@ -180,7 +195,7 @@ def make_plan(N, K, l, q, seed, B1=0, delta=1e-8, select_factor=2.0, min_votes=0
         raise ValueError("B1 must be a power of two in [16, min(4096, N/64)]")
     its = []
     for i, (B, Km) in enumerate(schedule(K, B1, max_iters)):
-        it = make_iteration(i + 1, N, n, B, l, qn, delta)
+        it = make_iteration(i + 1, N, n, B, l, qn, delta, location)
         it.n_c = min(B, int(math.ceil(select_factor * max(Km, 1.0))))
         its.append(it)
     for it in its:
@@ -188,4 +203,4 @@ def make_plan(N, K, l, q, seed, B1=0, delta=1e-8, select_factor=2.0, min_votes=0
             raise ValueError("window wider than N/2")
     return Plan(N=N, n=n, K=K, l=l, qn=qn, seed=seed, delta=delta, B1=B1,
                 select_factor=select_factor, min_votes=min_votes, sig_floor=sig_floor,
-                mag_tol=mag_tol, iters=its)
+                mag_tol=mag_tol, iters=its, location=location)

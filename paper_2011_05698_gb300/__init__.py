@@ -46,7 +46,8 @@ def _stream_ptr(device):
 
 
 def _opts(B1=0, delta=1e-8, precision="fp32", min_votes=0, select_factor=2.0, sig_floor=1e-10,
-          mag_tol=0.5, max_iters=64, max_batch=1, trace=False, profile=False, graph=False):
+          mag_tol=0.5, max_iters=64, max_batch=1, trace=False, profile=False, graph=False,
+          location="multiscale"):
     o = _lib.Opts()
     check(_lib.load().sfft4_opts_default(ctypes.byref(o)), "sfft4_opts_default")
     o.B1 = B1
@@ -61,6 +62,7 @@ def _opts(B1=0, delta=1e-8, precision="fp32", min_votes=0, select_factor=2.0, si
     o.trace = int(bool(trace))
     o.profile = int(bool(profile))
     o.graph = int(bool(graph))
+    o.location = {"multiscale": _lib.SFFT4_LOC_MULTISCALE, "two_round": _lib.SFFT4_LOC_TWO_ROUND}[location]
     return o
 
 
@@ -72,16 +74,18 @@ def _device(device):
 
 
 class Plan:
-    """A static sFFT4.0 plan (Section 3.1) for one (N, K, l, q, seed)."""
+    """A static sFFT4.0 plan (Section 3.1) for one (N, K, l, q, seed).  location="two_round"
+    replaces the multiscale location by the two-round (tau = 0, 1) location of sFFT3.0 for
+    exactly sparse signals."""
 
     def __init__(self, N, K, l=16, q=1.0, seed=0, *, B1=0, delta=1e-8, precision="fp32",
                  min_votes=0, select_factor=2.0, sig_floor=1e-10, mag_tol=0.5, max_iters=64,
-                 max_batch=1, trace=False, profile=False, graph=False, device=None):
+                 max_batch=1, trace=False, profile=False, graph=False, location="multiscale", device=None):
         import torch
         lib = _lib.load()
         self.device = _device(device)
         o = _opts(B1, delta, precision, min_votes, select_factor, sig_floor, mag_tol, max_iters,
-                  max_batch, trace, profile, graph)
+                  max_batch, trace, profile, graph, location)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             check(lib.sfft4_plan(ctypes.byref(h), N, K, l, q, seed, ctypes.byref(o)), "sfft4_plan")
@@ -223,7 +227,7 @@ class BatchPlan:
 
     def __init__(self, Ns, Ks, l=16, q=1.0, seed=0, *, B1=0, B1s=None, delta=1e-8, precision="fp32",
                  min_votes=0, select_factor=2.0, sig_floor=1e-10, mag_tol=0.5, max_iters=64,
-                 profile=False, graph=False, device=None):
+                 profile=False, graph=False, location="multiscale", device=None):
         import torch
         lib = _lib.load()
         self.device = _device(device)
@@ -232,7 +236,7 @@ class BatchPlan:
         if len(Ns) != len(Ks) or not Ns:
             raise ValueError("Ns and Ks must be non-empty and of equal length")
         o = _opts(B1, delta, precision, min_votes, select_factor, sig_floor, mag_tol, max_iters,
-                  1, False, profile, graph)
+                  1, False, profile, graph, location)
         nsig = len(Ns)
         Na = (ctypes.c_int64 * nsig)(*Ns)
         Ka = (ctypes.c_int64 * nsig)(*Ks)

@@ -497,6 +497,15 @@ __device__ __forceinline__ uint32_t phase_fixed(float2 ys, float2 y0) {
     return (uint32_t)f2ll_rn(turns * 4294967296.0f);
 }
 
+// Phase of ys conj(y0) in 2^-32 turns from FP64 products and atan2 (the final level of the
+// two-round location, whose integers are 2^(32-n) units apart).
+__device__ __noinline__ uint32_t phase_fixed64(float2 ys, float2 y0) {
+    const double cr = (double)ys.x * y0.x + (double)ys.y * y0.y;
+    const double cim = (double)ys.y * y0.x - (double)ys.x * y0.y;
+    const double turns = atan2(cim, cr) * 0.15915494309189533577;
+    return (uint32_t)llrint(turns * 4294967296.0);
+}
+
 // Radix select over 32-bit keys held one chunk per thread: returns the value T of the
 // n-th largest key (1 <= n <= count) by four passes over 8-bit digits, most significant
 // first.  hist must hold 256 ints of shared memory; all threads of the block call it.
@@ -920,6 +929,13 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig) 
 #pragma unroll
         for (int s = 1; s < RMAX; ++s)
             if (s == S) phS = ph[s - 1];
+        if (a.fine_phase) {
+            // phase step 1/N: FP32 atan2 is too coarse past N ~ 2^20
+            phS = phase_fixed64(Y[(int64_t)S * B + b], y0);
+#pragma unroll
+            for (int s = 1; s < RMAX; ++s)
+                if (s == S) ph[s - 1] = phS;
+        }
         uint32_t ustar;
         {
             const uint32_t ts = (uint32_t)it->tau[S];
@@ -1234,6 +1250,7 @@ DecodeArgs make_decode_args(const sfft4_plan_s* p, int mi) {
     a.l = p->l;
     a.qn = p->qn;
     a.min_votes = p->o.min_votes;
+    a.fine_phase = p->o.location == SFFT4_LOC_TWO_ROUND;
     a.mag_tol = (float)p->o.mag_tol;
     a.sig_floor = (float)p->o.sig_floor;
     a.it = p->iters_dev + mi;

@@ -196,9 +196,14 @@ int plan_options(int64_t N, int64_t K, int32_t l, double q, const sfft4_opts* op
     if (o.max_batch < 1 || o.max_iters < 1 || o.max_iters > 256) return SFFT4_EINVAL;
     if (!(o.select_factor > 0) || !(o.mag_tol > 0) || o.min_votes < 0) return SFFT4_EINVAL;
     if (o.l2_fetch_bytes > 128) return SFFT4_EINVAL;
+    if (o.location != SFFT4_LOC_MULTISCALE && o.location != SFFT4_LOC_TWO_ROUND) return SFFT4_EINVAL;
+    // the two-round vote window is 1/(8N) turns: FP32 bucket arrays resolve it up to N = 2^20
+    if (o.location == SFFT4_LOC_TWO_ROUND && N > (int64_t(1) << 20)) return SFFT4_EINVAL;
     int64_t B1 = o.B1;
     if (B1 == 0) {
-        B1 = std::max<int64_t>(kBMin, std::min<int64_t>({(int64_t)kBMax, N / 64, pow2ceil(2 * K)}));
+        // two-round location tolerates few collisions: default 8 K buckets instead of 2 K
+        const int64_t per = o.location == SFFT4_LOC_TWO_ROUND ? 8 : 2;
+        B1 = std::max<int64_t>(kBMin, std::min<int64_t>({(int64_t)kBMax, N / 64, pow2ceil(per * K)}));
         // halve the default until the window of B1 buckets fits in N/2 (schedule of Section 3.1)
         while (B1 > kBMin && 2 * window_halfwidth(B1, o.delta, nullptr) + 1 > N / 2) B1 >>= 1;
     }
@@ -232,13 +237,25 @@ int plan_schedule(sfft4_plan_s* p) {
         d.h = (int32_t)window_halfwidth(B, o.delta, nullptr);
         if (2 * (int64_t)d.h + 1 > N / 2) return SFFT4_EINVAL;
         // search region [bL - L, bL + L): pass band plus the transition bands (reading R5')
-        std::vector<int64_t> lv = levels(2 * d.L, l, qn);
-        int S = (int)lv.size();
+        if (o.location == SFFT4_LOC_TWO_ROUND) {
+            // rounds tau = 0, 1: the 2L integers of the search region compete directly, phase
+            // step 1/N; a lone tone's phase sits on an integer, so the vote takes 1/8 of it
+            d.S = 1;
+            d.R = 2;
+            d.Lbar[0] = 2 * d.L;
+            d.tau[0] = 0;
+            d.tau[1] = 1;
+            d.W[0] = (uint64_t)1 << (32 - p->n);
+            d.H[0] = (uint32_t)(d.W[0] / 8);
+            d.jscale[0] = (float)(1.0 / (double)d.W[0]);
+        }
+        std::vector<int64_t> lv = o.location == SFFT4_LOC_TWO_ROUND ? std::vector<int64_t>() : levels(2 * d.L, l, qn);
+        int S = o.location == SFFT4_LOC_TWO_ROUND ? 1 : (int)lv.size();
         if (S + 1 > kMaxRounds) return SFFT4_EINVAL;
         d.S = S;
         d.R = S + 1;
-        d.tau[0] = 0;
-        for (int s = 0; s < S; ++s) {
+        if (o.location != SFFT4_LOC_TWO_ROUND) d.tau[0] = 0;
+        for (int s = 0; s < (int)lv.size(); ++s) {
             int64_t Lb = lv[s];
             d.Lbar[s] = Lb;
             int64_t ts;

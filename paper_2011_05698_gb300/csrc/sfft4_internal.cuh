@@ -93,6 +93,7 @@ struct FoldTile {
 struct DecodeArgs {
     uint64_t N, seed;
     int32_t n, signal0, first, l, qn, min_votes;
+    int32_t fine_phase;   // final level's phase in FP64 (two-round location: step 1/N)
     float mag_tol, sig_floor;
     const IterDev* it;
     float2* y;

@@ -155,3 +155,15 @@ def test_autotune_candidates():
     assert autotune.candidates(2**16, 600) == [512, 1024]          # capped at N/64
     assert autotune.candidates(2**14, 4) == [16]                   # floor at 16
     assert all(b & (b - 1) == 0 for b in autotune.candidates(2**20, 77))
+
+
+def test_two_round_location_limits(lib):
+    from paper_2011_05698_gb300 import _lib
+    o = _lib.Opts()
+    lib.sfft4_opts_default(ctypes.byref(o))
+    h = ctypes.c_void_p()
+    o.location = 2
+    assert lib.sfft4_plan(ctypes.byref(h), 2**14, 16, 4, 0.5, 0, ctypes.byref(o)) == _lib.SFFT4_EINVAL
+    o.location = _lib.SFFT4_LOC_TWO_ROUND
+    assert lib.sfft4_plan(ctypes.byref(h), 2**21, 16, 16, 1.0, 0, ctypes.byref(o)) == _lib.SFFT4_EINVAL
+    assert not h.value

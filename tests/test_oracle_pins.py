@@ -407,3 +407,45 @@ def test_uneven_sizes_recipe():
     assert len(set(Ns.tolist())) == 7
     for N, K in sorted(set(zip(Ns.tolist(), Ks.tolist()))):
         P.make_plan(N, K, 16, 1.0, seed=0)
+
+
+@pytest.mark.parametrize("N,K,l,q", [(2**14, 16, 4, 0.5), (2**20, 100, 16, 1.0)])
+def test_two_round_location_exact_when_collisions_are_rare(N, K, l, q):
+    """The two-round (sFFT3.0) location: rounds tau = 0, 1, the phase of yhat_1 / yhat_0 is
+    u / N; with its default 8 K buckets noiseless signals are recovered exactly."""
+    pl = P.make_plan(N, K, l, q, seed=4, location="two_round")
+    assert all(it.R == 2 and it.tau == [0, 1] and it.Lbar == [2 * it.L] for it in pl.iters)
+    assert pl.B1 == min(4096, N // 64, P.pow2ceil(8 * K))
+    for seed in range(2):
+        sig = sparse_signal(N, K, seed)
+        r = sfft4.run(sig.x.astype(np.complex128), P.make_plan(N, K, l, q, seed=seed, location="two_round"))
+        assert np.array_equal(r["f"], sig.freqs)
+
+
+def test_two_round_location_needs_few_collisions():
+    """With 2 K buckets (collisions common) the two-round location accepts mixtures of
+    colliding tones that the multiscale levels reject: multiscale stays exact, two-round
+    does not (the robustness difference between the two location schemes)."""
+    N, K = 2**20, 100
+    sig = sparse_signal(N, K, 0)
+    ms = sfft4.run(sig.x.astype(np.complex128), P.make_plan(N, K, 16, 1.0, seed=0, B1=128))
+    tr = sfft4.run(sig.x.astype(np.complex128), P.make_plan(N, K, 16, 1.0, seed=0, B1=128, location="two_round"))
+    assert np.array_equal(ms["f"], sig.freqs)
+    assert not np.array_equal(tr["f"], sig.freqs)
+
+
+def test_two_round_single_tones():
+    N = 2**11
+    pl = P.make_plan(N, 1, 4, 0.5, seed=2, location="two_round")
+    rng = np.random.default_rng(5)
+    n = np.arange(N)
+    for f in list(rng.choice(N, 40, replace=False)) + [0, N - 1]:
+        X = np.exp(2j * np.pi * rng.uniform())
+        x = X * np.exp(2j * np.pi * ((f * n) % N) / N)
+        r = sfft4.run(x, pl)
+        assert list(r["f"]) == [f] and abs(r["v"][0] - X) < 1e-9
+
+
+def test_two_round_location_limit():
+    with pytest.raises(ValueError):
+        P.make_plan(2**21, 100, 16, 1.0, seed=0, location="two_round")
