@@ -636,12 +636,15 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig) 
         // shared memory: bucket offsets, then per staged entry v (float2), f, G'^ (3), and the
         // rotated values c_r = v e^{2 pi i f o_r / N} of the current pass (kUpdRounds float2),
         // then (several splits per bucket) the splits' partial sums
-        const int splits = B < T ? min(8, T / B) : 1;
         const size_t off_v = ((size_t)4 * (2 * B + 1) + 7) & ~(size_t)7;
         const size_t off_c = off_v + (size_t)8 * F0;
         const size_t off_f = off_c + (size_t)8 * kUpdRounds * F0;
         const size_t off_g = off_f + (size_t)4 * F0;
         const size_t acc_off = (off_g + (size_t)12 * F0 + 15) & ~(size_t)15;
+        // splits per bucket: enough items for every thread when B < T, as many as the
+        // partial sums leave room for
+        int splits = B < T ? T / B : 1;
+        while (splits > 1 && acc_off + (size_t)16 * kUpdRounds * splits * B > decode_smem(B)) splits >>= 1;
         const size_t need = acc_off + (splits > 1 ? (size_t)16 * kUpdRounds * splits * B : 0);
         if (B <= kGatherMaxB && need <= decode_smem(B)) {
             int* cnt = (int*)smraw;          // B + 1: counts, then offsets of each bucket's entries
@@ -849,41 +852,63 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig) 
     __syncthreads();
     const float theta = s_theta;
     const int n_c = it->n_c;
-    // each thread owns a contiguous chunk of buckets for order-preserving scans
-    const int E = (B + T - 1) / T;
-    const int b_lo = min(B, tid * E), b_hi = min(B, b_lo + E);
-    uint32_t Tb = 0;
-    int need_ties = 0;
-    if (n_c < B) {
-        // T = the n_c-th largest key (keys >= 0 compare as unsigned integers)
-        Tb = block_radix_select(key, b_lo, b_hi, n_c, s_hist, s_bc);
-        int gt = 0;
-        for (int b = b_lo; b < b_hi; ++b) gt += (__float_as_uint(key[b]) > Tb);
-        need_ties = n_c - block_count(gt, &s_cnt);
-    }
-    // selection flags of this thread's chunk (E <= 4 buckets), ties to the lower b
-    int ties = 0;
-    for (int b = b_lo; b < b_hi; ++b) ties += (n_c < B && __float_as_uint(key[b]) == Tb);
-    int tot_ties;
-    int tie_rank = block_exscan(ties, s_ws, &tot_ties);
-    uint32_t selmask = 0;
-    int nsel_local = 0;
-    for (int b = b_lo; b < b_hi; ++b) {
-        const uint32_t kb = __float_as_uint(key[b]);
-        bool sel;
-        if (n_c >= B) sel = true;
-        else if (kb > Tb) sel = true;
-        else if (kb == Tb) { sel = tie_rank < need_ties; ++tie_rank; }
-        else sel = false;
-        sel = sel && (key[b] > theta);
-        if (sel) selmask |= 1u << (b - b_lo);
-        nsel_local += sel;
-    }
     int ncand;
-    int pos = block_exscan(nsel_local, s_ws, &ncand);
-    for (int b = b_lo; b < b_hi; ++b)
-        if ((selmask >> (b - b_lo)) & 1u) cand[pos++] = (uint16_t)b;
-    __syncthreads();
+    if (B <= 32) {
+        // one warp: the rank of each key (larger first, ties to the lower bucket) decides the
+        // same n_c buckets as the block-wide radix select below
+        if (tid < 32) {
+            const int b = tid;
+            const bool valid = b < B;
+            const uint32_t kb = valid ? __float_as_uint(key[b]) : 0u;
+            int rank = 0;
+            for (int j = 0; j < 32; ++j) {
+                const uint32_t kj = __shfl_sync(0xffffffffu, kb, j);
+                rank += (j < B) && (kj > kb || (kj == kb && j < b));
+            }
+            const bool sel = valid && (n_c >= B || rank < n_c) && key[b] > theta;
+            const unsigned m = __ballot_sync(0xffffffffu, sel);
+            if (sel) cand[__popc(m & ((1u << b) - 1u))] = (uint16_t)b;
+            if (tid == 0) s_bc[0] = __popc(m);
+        }
+        __syncthreads();
+        ncand = s_bc[0];
+        __syncthreads();
+    } else {
+        // each thread owns a contiguous chunk of buckets for order-preserving scans
+        const int E = (B + T - 1) / T;
+        const int b_lo = min(B, tid * E), b_hi = min(B, b_lo + E);
+        uint32_t Tb = 0;
+        int need_ties = 0;
+        if (n_c < B) {
+            // T = the n_c-th largest key (keys >= 0 compare as unsigned integers)
+            Tb = block_radix_select(key, b_lo, b_hi, n_c, s_hist, s_bc);
+            int gt = 0;
+            for (int b = b_lo; b < b_hi; ++b) gt += (__float_as_uint(key[b]) > Tb);
+            need_ties = n_c - block_count(gt, &s_cnt);
+        }
+        // selection flags of this thread's chunk (E <= 4 buckets), ties to the lower b
+        int ties = 0;
+        for (int b = b_lo; b < b_hi; ++b) ties += (n_c < B && __float_as_uint(key[b]) == Tb);
+        int tot_ties;
+        int tie_rank = block_exscan(ties, s_ws, &tot_ties);
+        uint32_t selmask = 0;
+        int nsel_local = 0;
+        for (int b = b_lo; b < b_hi; ++b) {
+            const uint32_t kb = __float_as_uint(key[b]);
+            bool sel;
+            if (n_c >= B) sel = true;
+            else if (kb > Tb) sel = true;
+            else if (kb == Tb) { sel = tie_rank < need_ties; ++tie_rank; }
+            else sel = false;
+            sel = sel && (key[b] > theta);
+            if (sel) selmask |= 1u << (b - b_lo);
+            nsel_local += sel;
+        }
+        int pos = block_exscan(nsel_local, s_ws, &ncand);
+        for (int b = b_lo; b < b_hi; ++b)
+            if ((selmask >> (b - b_lo)) & 1u) cand[pos++] = (uint16_t)b;
+        __syncthreads();
+    }
 
     // ---- 3. multiscale location, votes, estimation: one thread per candidate ----------
     const int l = a.l;
