@@ -223,6 +223,16 @@ def uneven_form(s4, args, dev, stream, dist):
     world = dist.get_world_size() if dist is not None else 1
     info = dict(bp.info)
     bp.close()
+    # the same launches issued directly (no graph), for comparison
+    direct = None
+    if graph:
+        bd = s4.BatchPlan(Ns.tolist(), Ks.tolist(), L_DEF, Q_DEF, seed=seed, precision=args.precision, B1s=B1s)
+        outd = bd.outputs()
+        ptrd = bd.pointers(xs)
+        ed = max_over_ranks(timed(lambda: bd.execute(xs, out=outd, ptrs=ptrd), steps, args.warmup, stream, dist),
+                            dist, dev)
+        direct = {"value": nsig * steps * world / ed, "ms_per_step": 1e3 * ed / steps}
+        bd.close()
     bq = s4.BatchPlan(Ns.tolist(), Ks.tolist(), L_DEF, Q_DEF, seed=seed, precision=args.precision, profile=True,
                       B1s=B1s)
     outq = bq.outputs()
@@ -239,7 +249,7 @@ def uneven_form(s4, args, dev, stream, dist):
             "graph_launches_per_step": 1 if graph else 0, "levels": info["n_levels"], "classes": info["n_classes"],
             "workload": "512 signals: N=2^n, n uniform on 16..22; K=round(exp U[ln 10, ln 2000]) <= N/64; "
                         "SNR U[10, 40] dB; l=16, q=1",
-            "fold_gbs_useful": fold_gbs, "autotune": tune,
+            "fold_gbs_useful": fold_gbs, "autotune": tune, "direct_launches": direct,
             "kernel_ms_one_execute": {k: prof[k + "_ms"] for k in ("fold", "fft", "decode", "finalize")}}
 
 

@@ -194,15 +194,16 @@ int build_group_plan(sfft4_plan_s* p, int nsig, const int64_t* Ns, const int64_t
     std::vector<int32_t> dlist;
     for (int mi = 0; mi < Mmax; ++mi) {
         GroupLevel L;
-        // fold tiles by round count of the group (register accumulators)
-        for (int RG = 1; RG <= kFoldRG; ++RG) {
-            GroupLevel::Fold f{RG, (int64_t)tiles.size(), 0, 0, 0, 0};
+        // fold tiles of every signal and fold group of the level in one launch, instantiated for
+        // the level's largest rounds-per-group count (a group with fewer rounds leaves the extra
+        // register accumulators unused; its arithmetic is unchanged)
+        {
+            GroupLevel::Fold f{1, (int64_t)tiles.size(), 0, 0, 0, 0};
             for (int i = 0; i < nsig; ++i) {
                 const sfft4_plan_s* c = g->cls[g->slot_cls[i]];
                 if (mi >= (int)c->iters.size()) continue;
                 const IterHost& ih = c->iters[mi];
                 for (const FoldGroup& fg : ih.groups) {
-                    if (fg.nr != RG) continue;
                     size_t smem = 0;
                     FoldArgs a = make_fold_args(c, mi, fg, &smem);
                     a.z = (float2*)(A + so[i].z);
@@ -210,6 +211,7 @@ int build_group_plan(sfft4_plan_s* p, int nsig, const int64_t* Ns, const int64_t
                     const int job = (int)fjobs.size();
                     fjobs.push_back(a);
                     for (int sl = 0; sl < ih.d.B / ih.Wj; ++sl) tiles.push_back({job, sl});
+                    f.RG = std::max(f.RG, (int)fg.nr);
                     f.threads = std::max(f.threads, ih.Wj * fg.P);
                     f.smem = std::max(f.smem, smem);
                     f.samples += fg.unique;
