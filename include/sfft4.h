@@ -151,9 +151,10 @@ SFFT4_API int sfft4_execute_batched(sfft4_plan_t plan, int32_t nsig, const void*
  *               e.g. chosen per (N, K) by an autotuner); overrides opts->B1
  *   l, q, seed, opts  as for sfft4_plan, shared by every signal (opts.max_batch is ignored)
  * Signals with equal (N, K, B1) share one schedule; window tables are shared by (N, B).  Level m
- * of an execute runs iteration m of every signal that has one, as one fold launch per
- * rounds-per-group count, one DFT launch per bucket count and one decode launch per
- * round-count class, taking their work from job tables built here.  Signal i uses Philox
+ * of an execute runs iteration m of every signal that has one, as one fold launch, one or two
+ * tensor-core DFT launches (one FP32 DFT launch per bucket count) and one decode launch per
+ * round-count class, taking their work from job tables built here; the decode chain runs on
+ * a second stream beside the bucketization of later levels.  Signal i uses Philox
  * counter (i, m, 0, 0), so it matches sfft4_plan(N[i], K[i], ...) run as signal i.
  * Errors: SFFT4_EINVAL (NULL pointers, nsig < 1, any size invalid), SFFT4_ENOMEM, SFFT4_ECUDA.
  */
@@ -184,6 +185,26 @@ typedef struct {
     int64_t samples_per_execute;  /* distinct x positions read, summed over signals */
     int32_t precision;
 } sfft4_batch_info;
+
+#define SFFT4_MAX_VOTES 64
+typedef struct {
+    int64_t executes;            /* executes since the plan was made */
+    int64_t transforms;          /* signals transformed since then */
+    int64_t samples_per_execute; /* distinct x positions the last execute read (all signals) */
+    int32_t iterations;          /* iterations (levels) of the longest schedule */
+    int32_t kernels_per_execute; /* kernel launches of one execute */
+    int32_t last_nsig;           /* signals of the last execute */
+    int32_t reserved;
+    int64_t last_found;          /* found-set entries after the last execute, all signals */
+    int64_t votes_hist[SFFT4_MAX_VOTES + 1];  /* of those: how many were accepted with v votes */
+} sfft4_run_stats;
+
+/*
+ * sfft4_stats -- counters of a plan (either kind) and the votes of the last execute's found
+ * sets (levels that voted when each frequency was first accepted, Section 3.2).  Synchronises
+ * the device.  Errors: SFFT4_EINVAL (NULL pointers), SFFT4_ECUDA.
+ */
+SFFT4_API int sfft4_stats(sfft4_plan_t plan, sfft4_run_stats* out);
 
 /* Summary of a plan from sfft4_plan_batched.  Errors: SFFT4_EINVAL, SFFT4_ESTATE. */
 SFFT4_API int sfft4_get_batch_info(sfft4_plan_t plan, sfft4_batch_info* info);

@@ -145,6 +145,14 @@ class Plan:
         """Synchronise and raise if a bounded device wait of this plan gave up."""
         check(_lib.load().sfft4_sync_status(self._h), "sfft4_sync_status")
 
+    def stats(self):
+        """Counters and the votes histogram of the last execute's found sets (synchronises)."""
+        st = _lib.RunStats()
+        check(_lib.load().sfft4_stats(self._h, ctypes.byref(st)), "sfft4_stats")
+        d = {k: getattr(st, k) for k, _ in _lib.RunStats._fields_ if k not in ("votes_hist", "reserved")}
+        d["votes_hist"] = list(st.votes_hist)
+        return d
+
     def profile(self, reset=True):
         """Per-kernel launch counts and CUDA-event times since the last reset (profile=True)."""
         pr = _lib.Profile()
@@ -276,6 +284,14 @@ class BatchPlan:
 
     def sync_status(self):
         check(_lib.load().sfft4_sync_status(self._h), "sfft4_sync_status")
+
+    def stats(self):
+        """Counters and the votes histogram of the last execute's found sets (synchronises)."""
+        st = _lib.RunStats()
+        check(_lib.load().sfft4_stats(self._h, ctypes.byref(st)), "sfft4_stats")
+        d = {k: getattr(st, k) for k, _ in _lib.RunStats._fields_ if k not in ("votes_hist", "reserved")}
+        d["votes_hist"] = list(st.votes_hist)
+        return d
 
     def profile(self, reset=True):
         pr = _lib.Profile()

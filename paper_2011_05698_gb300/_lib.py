@@ -42,6 +42,14 @@ class BatchInfo(ctypes.Structure):
                 ("samples_per_execute", ctypes.c_int64), ("precision", ctypes.c_int32)]
 
 
+class RunStats(ctypes.Structure):
+    _fields_ = [("executes", ctypes.c_int64), ("transforms", ctypes.c_int64),
+                ("samples_per_execute", ctypes.c_int64), ("iterations", ctypes.c_int32),
+                ("kernels_per_execute", ctypes.c_int32), ("last_nsig", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("last_found", ctypes.c_int64),
+                ("votes_hist", ctypes.c_int64 * 65)]
+
+
 class IterInfo(ctypes.Structure):
     _fields_ = [("B", ctypes.c_int32), ("S", ctypes.c_int32), ("n_c", ctypes.c_int32),
                 ("h", ctypes.c_int32), ("L", ctypes.c_int64),
@@ -88,6 +96,7 @@ SIGNATURES = [
     ("sfft4_window_noalloc", ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_double, _P,
                                             ctypes.c_int64, _P, ctypes.c_int64, _P]),
     ("sfft4_sync_status", ctypes.c_int, [_P]),
+    ("sfft4_stats", ctypes.c_int, [_P, ctypes.POINTER(RunStats)]),
     ("sfft4_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("sfft4_last_cuda_error", ctypes.c_char_p, []),
 ]

@@ -109,6 +109,13 @@ void destroy_group(Group* g) { free_group(g); }
 
 size_t group_levels(const Group* g) { return g->levels.size(); }
 
+const FinalJob* group_final_jobs(const Group* g, int* nsig, int64_t* samples, int* kernels) {
+    *nsig = g->nsig;
+    *samples = g->samples;
+    *kernels = g->kernels;
+    return g->fin_jobs;
+}
+
 int build_group_plan(sfft4_plan_s* p, int nsig, const int64_t* Ns, const int64_t* Ks, const int32_t* B1s,
                      int32_t l, double q, uint64_t seed, const sfft4_opts* opts) {
     Group* g = new (std::nothrow) Group();
@@ -382,7 +389,12 @@ int sfft4_execute_batched_v(sfft4_plan_t p, const void* const* x_ptrs_dev, int64
                              (uint64_t)(uintptr_t)val_dev, (uint64_t)(uintptr_t)nfound_dev,
                              (uint64_t)(uintptr_t)votes_dev, 0, 0};
     int rc = graph_run(p, key, (cudaStream_t)stream, group_body, &r);
-    if (!rc) p->executed = true;
+    if (!rc) {
+        p->executed = true;
+        ++p->n_executes;
+        p->n_transforms += p->grp->nsig;
+        p->last_nsig = p->grp->nsig;
+    }
     return rc;
 }
 

@@ -1176,6 +1176,23 @@ __global__ void __launch_bounds__(1024) k_finalize_multi(const FinalJob* __restr
                   blockIdx.x);
 }
 
+// Histogram of the votes of every found-set entry of jobs[blockIdx.x]'s signal.
+__global__ void __launch_bounds__(256) k_votes_hist(const FinalJob* __restrict__ jobs,
+                                                    unsigned long long* __restrict__ hist) {
+    __shared__ unsigned int h[SFFT4_MAX_VOTES + 1];
+    for (int i = threadIdx.x; i <= SFFT4_MAX_VOTES; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const FinalJob j = jobs[blockIdx.x];
+    const int F = *j.F;
+    for (int e = threadIdx.x; e < F; e += blockDim.x) {
+        const int v = j.fvt[e];
+        atomicAdd(&h[v < 0 ? 0 : (v > SFFT4_MAX_VOTES ? SFFT4_MAX_VOTES : v)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= SFFT4_MAX_VOTES; i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
+}
+
 // ----------------------------------------------------------------- launchers --------
 int configure_kernels();
 
@@ -1355,6 +1372,12 @@ int launch_finalize_multi(const FinalJob* jobs, int nsig, int64_t Kout, int64_t*
     while (P2 < Kout) P2 <<= 1;
     size_t smem = (size_t)P2 * sizeof(unsigned long long);
     k_finalize_multi<<<nsig, 1024, smem, st>>>(jobs, Kout, idx, val, nfound, votes);
+    return check_cuda(cudaGetLastError());
+}
+
+int launch_votes_hist(const FinalJob* jobs, int nsig, unsigned long long* hist, cudaStream_t st) {
+    if (nsig < 1) return SFFT4_OK;
+    k_votes_hist<<<nsig, 256, 0, st>>>(jobs, hist);
     return check_cuda(cudaGetLastError());
 }
 
@@ -1547,7 +1570,12 @@ int run(sfft4_plan_s* p, int nsig, const float2* x, int64_t x_stride, int64_t* i
                              (uint64_t)(uintptr_t)idx, (uint64_t)(uintptr_t)val,
                              (uint64_t)(uintptr_t)nfound, (uint64_t)(uintptr_t)votes};
     int rc = graph_run(p, key, st, run_body, &r);
-    if (!rc) p->executed = true;
+    if (!rc) {
+        p->executed = true;
+        ++p->n_executes;
+        p->n_transforms += nsig;
+        p->last_nsig = nsig;
+    }
     return rc;
 }
 }  // namespace
@@ -1578,6 +1606,60 @@ int sfft4_bucketize(sfft4_plan_t p, const void* x_dev, int32_t signal, int32_t m
     const IterDev& d = p->iters[m - 1].d;
     return launch_bucketize(p, m - 1, 1, (const float2*)x_dev, p->N, signal, (float2*)y_dev,
                             (int64_t)d.R * d.B, (cudaStream_t)stream);
+}
+
+int sfft4_stats(sfft4_plan_t p, sfft4_run_stats* out) {
+    if (!p || !out) return SFFT4_EINVAL;
+    memset(out, 0, sizeof(*out));
+    out->executes = p->n_executes;
+    out->transforms = p->n_transforms;
+    out->last_nsig = p->last_nsig;
+    std::vector<FinalJob> jobs;
+    if (p->grp) {
+        int n = 0, kern = 0;
+        int64_t samples = 0;
+        group_final_jobs(p->grp, &n, &samples, &kern);
+        out->samples_per_execute = samples;
+        out->iterations = (int32_t)group_levels(p->grp);
+        out->kernels_per_execute = kern;
+    } else {
+        out->samples_per_execute = p->samples * p->last_nsig;
+        out->iterations = (int32_t)p->iters.size();
+        out->kernels_per_execute = uniform_kernels(p);
+        for (int s = 0; s < p->last_nsig; ++s)
+            jobs.push_back(FinalJob{p->F + s, p->ff + (int64_t)s * p->Fcap, p->fv + (int64_t)s * p->Fcap,
+                                    p->fvotes + (int64_t)s * p->Fcap, p->Fcap, p->K});
+    }
+    if (!p->executed) return SFFT4_OK;
+    int rc = check_cuda(cudaDeviceSynchronize());
+    if (rc) return rc;
+    const FinalJob* djobs = nullptr;
+    FinalJob* tmp = nullptr;
+    int nj = 0;
+    if (p->grp) {
+        int64_t samples;
+        int kern;
+        djobs = group_final_jobs(p->grp, &nj, &samples, &kern);
+    } else {
+        nj = (int)jobs.size();
+        rc = check_cuda(cudaMalloc(&tmp, jobs.size() * sizeof(FinalJob)));
+        if (!rc) rc = check_cuda(cudaMemcpy(tmp, jobs.data(), jobs.size() * sizeof(FinalJob), cudaMemcpyHostToDevice));
+        djobs = tmp;
+    }
+    unsigned long long* dh = nullptr;
+    if (!rc) rc = check_cuda(cudaMalloc(&dh, (SFFT4_MAX_VOTES + 1) * sizeof(unsigned long long)));
+    if (!rc) rc = check_cuda(cudaMemset(dh, 0, (SFFT4_MAX_VOTES + 1) * sizeof(unsigned long long)));
+    if (!rc) rc = launch_votes_hist(djobs, nj, dh, 0);
+    unsigned long long hh[SFFT4_MAX_VOTES + 1] = {0};
+    if (!rc) rc = check_cuda(cudaMemcpy(hh, dh, sizeof(hh), cudaMemcpyDeviceToHost));
+    cudaFree(dh);
+    cudaFree(tmp);
+    if (rc) return rc;
+    for (int v = 0; v <= SFFT4_MAX_VOTES; ++v) {
+        out->votes_hist[v] = (int64_t)hh[v];
+        out->last_found += (int64_t)hh[v];
+    }
+    return SFFT4_OK;
 }
 
 int sfft4_sync_status(sfft4_plan_t p) {

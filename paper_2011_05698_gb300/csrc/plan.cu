@@ -173,6 +173,15 @@ int sfft4_opts_default(sfft4_opts* o) {
 
 namespace sfft4 {
 
+// Kernel launches of one execute of a uniform plan: per iteration its fold groups, one FP32 DFT
+// or one/two tensor-core DFT stages, one decode; one finalize.
+int32_t uniform_kernels(const sfft4_plan_s* p) {
+    int32_t k = 1;
+    for (auto& ih : p->iters)
+        k += (int32_t)ih.groups.size() + 1 + ((p->o.precision == SFFT4_BF16X3 && ih.d.B > 64) ? 2 : 1);
+    return k;
+}
+
 // Options with zero fields replaced by defaults, validated with the sizes (sfft4_plan's checks).
 int plan_options(int64_t N, int64_t K, int32_t l, double q, const sfft4_opts* opts, sfft4_opts* out,
                  int* qn_out) {
@@ -502,9 +511,7 @@ int sfft4_get_plan_info(sfft4_plan_t p, sfft4_plan_info* info) {
     info->precision = p->o.precision;
     info->samples_per_transform = p->samples;
     info->found_capacity = p->Fcap;
-    int32_t kpe = 1;  // finalize
-    for (auto& ih : p->iters) kpe += (int32_t)ih.groups.size() + 2;
-    info->kernels_per_execute = kpe;
+    info->kernels_per_execute = uniform_kernels(p);
     return SFFT4_OK;
 }
 

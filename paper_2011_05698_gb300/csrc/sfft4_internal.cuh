@@ -216,6 +216,8 @@ struct sfft4_plan_s {
     double2* trace_fv = nullptr;    // [iter][Fcap]
     int8_t* trace_votes = nullptr;  // [iter][Fcap]
     bool executed = false;
+    int64_t n_executes = 0, n_transforms = 0;  // counters (sfft4_stats)
+    int32_t last_nsig = 0;
     bool owns_tables = true;    // false when the window tables belong to a batch's cache
     sfft4::Group* grp = nullptr;  // set for plans from sfft4_plan_batched
     // CUDA graph of the last captured execute (opts.graph), keyed on its buffers
@@ -260,6 +262,7 @@ int launch_decode_multi(int rclass, const DecodeArgs* jobs, const int32_t* list,
                         cudaStream_t st);
 int launch_finalize_multi(const FinalJob* jobs, int nsig, int64_t Kout, int64_t* idx, sfft4_c128* val,
                           int64_t* nfound, int8_t* votes, cudaStream_t st);
+int launch_votes_hist(const FinalJob* jobs, int nsig, unsigned long long* hist, cudaStream_t st);
 int prof_begin(sfft4_plan_s* p, cudaStream_t st, cudaEvent_t* a);
 int prof_end(sfft4_plan_s* p, cudaStream_t st, cudaEvent_t a, int kind, int64_t samples);
 enum { kProfFold = 0, kProfFft = 1, kProfDecode = 2, kProfFinalize = 3 };
@@ -273,10 +276,12 @@ int build_group_plan(sfft4_plan_s* p, int nsig, const int64_t* N, const int64_t*
                      double q, uint64_t seed, const sfft4_opts* opts);
 void destroy_group(Group* g);
 size_t group_levels(const Group* g);
+const FinalJob* group_final_jobs(const Group* g, int* nsig, int64_t* samples, int* kernels);
 // Implemented in plan.cu.
 int plan_options(int64_t N, int64_t K, int32_t l, double q, const sfft4_opts* opts, sfft4_opts* out,
                  int* qn_out);
 int plan_schedule(sfft4_plan_s* p);
+int32_t uniform_kernels(const sfft4_plan_s* p);
 int plan_tables(sfft4_plan_s* p, std::vector<Window>* cache);
 // Implemented in dft_tc.cu.
 size_t dft_tc_matrix_bytes();

@@ -235,3 +235,18 @@ def test_uneven_workload_full_size_sampled(s4):
         gi, oi = np.searchsorted(f, common), np.searchsorted(r["f"], common)
         assert np.linalg.norm(v[gi] - r["v"][oi]) <= 1e-4 * np.linalg.norm(r["v"][oi]), i
     bp.close()
+
+
+def test_batch_stats(s4):
+    sizes = [(2**16, 50), (2**14, 16), (2**16, 50)]
+    sigs = mixed_signals(sizes, 12)
+    bp = s4.BatchPlan([n for n, _ in sizes], [k for _, k in sizes], L_, Q_, seed=12)
+    idx, val, nf, votes = bp.execute([to_dev(s.x) for s in sigs])
+    st = bp.stats()
+    assert st["executes"] == 1 and st["transforms"] == 3 and st["last_found"] == int(nf.sum()) == 116
+    assert st["samples_per_execute"] == bp.info["samples_per_execute"]
+    h = np.zeros(65, np.int64)
+    for i, (_, K) in enumerate(sizes):
+        h += np.bincount(votes[i, :K].cpu().numpy().astype(np.int64), minlength=65)
+    assert list(h) == st["votes_hist"]
+    bp.close()

@@ -284,3 +284,26 @@ def test_single_tones(s4):
         assert int(nf) == 1 and int(idx[0]) == f
         assert abs(complex(val[0].item()) - X) < 2e-6
     p.close()
+
+
+def test_stats_counts_and_votes_histogram(s4):
+    """sfft4_stats: execute and transform counters, samples, and a votes histogram of the
+    last execute's found sets that agrees with the votes the execute returned (noiseless:
+    the found sets hold exactly the K true frequencies)."""
+    import torch
+    N, K, l, q, B1 = CONFIGS["c2"]
+    sigs = [sparse_signal(N, K, 200 + i, None) for i in range(3)]
+    xs = torch.stack([to_dev(s.x) for s in sigs])
+    p = s4.Plan(N, K, l, q, seed=7, B1=B1, max_batch=4)
+    st0 = p.stats()
+    assert st0["executes"] == 0 and st0["last_found"] == 0
+    p.execute_batched(xs)
+    idx, val, nf, votes = p.execute_batched(xs)
+    st = p.stats()
+    assert st["executes"] == 2 and st["transforms"] == 6 and st["last_nsig"] == 3
+    assert st["samples_per_execute"] == 3 * p.info["samples_per_transform"]
+    assert st["kernels_per_execute"] == p.info["kernels_per_execute"]
+    assert st["last_found"] == int(nf.sum()) == 3 * K
+    h = np.bincount(votes.cpu().numpy().ravel().astype(np.int64), minlength=65)  # every row holds K entries
+    assert list(h[:65]) == st["votes_hist"]
+    p.close()

@@ -48,17 +48,19 @@ def test_struct_layouts_match_c(tmp_path):
     from paper_2011_05698_gb300 import _lib
     src = tmp_path / "sz.c"
     src.write_text('#include "sfft4.h"\n#include <stdio.h>\n#include <stddef.h>\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(sfft4_opts), '
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(sfft4_opts), '
                    'sizeof(sfft4_plan_info), sizeof(sfft4_iter_info), offsetof(sfft4_iter_info, tau), '
                    'offsetof(sfft4_iter_info, unique_samples), sizeof(sfft4_c128), '
                    'offsetof(sfft4_opts, graph), sizeof(sfft4_batch_info), '
-                   'offsetof(sfft4_batch_info, samples_per_execute)); return 0;}\n')
+                   'offsetof(sfft4_batch_info, samples_per_execute), sizeof(sfft4_run_stats), '
+                   'offsetof(sfft4_run_stats, votes_hist), offsetof(sfft4_opts, location)); return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     want = [ctypes.sizeof(_lib.Opts), ctypes.sizeof(_lib.PlanInfo), ctypes.sizeof(_lib.IterInfo),
             _lib.IterInfo.tau.offset, _lib.IterInfo.unique_samples.offset, ctypes.sizeof(_lib.C128),
-            _lib.Opts.graph.offset, ctypes.sizeof(_lib.BatchInfo), _lib.BatchInfo.samples_per_execute.offset]
+            _lib.Opts.graph.offset, ctypes.sizeof(_lib.BatchInfo), _lib.BatchInfo.samples_per_execute.offset,
+            ctypes.sizeof(_lib.RunStats), _lib.RunStats.votes_hist.offset, _lib.Opts.location.offset]
     assert got == want
 
 
@@ -115,6 +117,7 @@ def test_execute_rejects_null_arguments(lib):
     assert lib.sfft4_trace_get(None, 1, None, 0, None, None, None, None) == _lib.SFFT4_EINVAL
     assert lib.sfft4_execute_batched_v(None, None, None, None, None, None, None) == _lib.SFFT4_EINVAL
     assert lib.sfft4_get_batch_info(None, None) == _lib.SFFT4_EINVAL
+    assert lib.sfft4_stats(None, None) == _lib.SFFT4_EINVAL
     lib.sfft4_destroy(None)
 
 
