@@ -156,12 +156,17 @@ def measured_peaks():
 
 
 def fold_source_sha256():
-    """sha256 of the fold kernel's source: kernels.cu from its fold section header up to the
-    FFT section header."""
-    src = open(os.path.join(ROOT, "paper_2011_05698_gb300", "csrc", "kernels.cu")).read()
+    """sha256 of what sets the fold's DRAM traffic: kernels.cu from its fold section header
+    up to the FFT section header, the signal-major launch builder, and plan.cu (residue
+    slices, copies, fold groups and the L2 fetch granularity)."""
+    csrc = os.path.join(ROOT, "paper_2011_05698_gb300", "csrc")
+    src = open(os.path.join(csrc, "kernels.cu")).read()
     a = src.index("// ----------------------------------------------------------------- fold")
     b = src.index("// ----------------------------------------------------------------- FFT")
-    return hashlib.sha256(src[a:b].encode()).hexdigest()
+    c = src.index("int build_signal_major_fold(")
+    d = src.index("int launch_fft_multi(")
+    plan = open(os.path.join(csrc, "plan.cu")).read()
+    return hashlib.sha256((src[a:b] + src[c:d] + plan).encode()).hexdigest()
 
 
 def fold_traffic_record():
@@ -483,6 +488,8 @@ def main():
     ap.add_argument("--plain-signals", type=int, default=16)
     ap.add_argument("--uneven-signals", type=int, default=512)
     ap.add_argument("--no-fp32-form", action="store_true")
+    ap.add_argument("--fold-order", default="signal_major", choices=["signal_major", "iteration_major"],
+                    help="fold order of the headline plan")
     ap.add_argument("--form", default="all", choices=["all", "uneven", "sweep", "configs", "phase_error"],
                     help="uneven: time only the uneven-batch form; sweep: the large-N SNR x (l, q) "
                          "sweep (N = 2^26, K = 4000, 10 seeds)")
@@ -543,7 +550,7 @@ def main():
 
     S = args.batch
     plan = s4.Plan(N_DEF, K_DEF, L_DEF, Q_DEF, seed=1234, max_batch=S, profile=True,
-                   precision=args.precision)
+                   precision=args.precision, fold_order=args.fold_order)
     xs = device_batch(N_DEF, K_DEF, S, rank_seed0(rank), args.snr, dev)
     out = plan._outputs(S)
     stream = torch.cuda.current_stream(dev)
@@ -729,6 +736,7 @@ def main():
                 "config": {"workload": WORKLOAD, "N": N_DEF, "K": K_DEF, "l": L_DEF, "q": Q_DEF,
                            "snr_db": args.snr, "batch_per_gpu": S, "B1": plan.info["B1"],
                            "iterations": plan.info["n_iters"], "precision": args.precision,
+                           "fold_order": args.fold_order,
                            "samples_per_transform": plan.info["samples_per_transform"],
                            "l2": "inputs larger than L2 (touched samples per step "
                                  f"{S * plan.info['samples_per_transform'] * 32 / 1e9:.1f} GB of 32 B sectors)",

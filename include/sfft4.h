@@ -42,10 +42,14 @@ extern "C" {
 
 /* ----------------------------------------------------------------- precision ------ */
 #define SFFT4_FP32 0        /* window, fold and B-point DFT in FP32 (CUDA cores)         */
-#define SFFT4_BF16X3 1
-#define SFFT4_LOC_MULTISCALE 0
-#define SFFT4_LOC_TWO_ROUND 1      /* B-point DFT as a BF16x3 split-precision complex GEMM on   */
+#define SFFT4_BF16X3 1      /* B-point DFT as a BF16x3 split-precision complex GEMM on   */
                             /* the tensor cores (tcgen05), FP32 accumulation             */
+
+/* ----------------------------------------------------------------- options -------- */
+#define SFFT4_LOC_MULTISCALE 0        /* sfft4_opts.location */
+#define SFFT4_LOC_TWO_ROUND 1
+#define SFFT4_FOLD_SIGNAL_MAJOR 0     /* sfft4_opts.fold_order */
+#define SFFT4_FOLD_ITERATION_MAJOR 1
 
 typedef struct sfft4_plan_s* sfft4_plan_t;   /* opaque, library-owned */
 
@@ -75,8 +79,9 @@ typedef struct {
                                 events on the execution stream (sfft4_profile_get)        */
     int32_t l2_fetch_bytes;  /* L2 fetch granularity hint the plan sets on the calling
                                 process's CUDA context (cudaLimitMaxL2FetchGranularity):
-                                0 = 32 bytes (one sector per gathered sample), negative =
-                                leave the context's limit unchanged                        */
+                                0 = 64 bytes (measured best for the signal-major fold),
+                                32 or 128 = that many bytes, negative = leave the context's
+                                limit unchanged                                            */
     int32_t graph;           /* nonzero: the first execute with a given set of buffers and
                                 batch size captures its launch sequence as a CUDA graph;
                                 later executes with the same buffers replay it (one graph
@@ -88,6 +93,13 @@ typedef struct {
                                 phase of yhat_1 / yhat_0 is u / N; exactly sparse signals with
                                 few collisions; default B1 pow2ceil(8K); N <= 2^20, where FP32
                                 bucket arrays resolve its 1/(8N)-turn vote window)          */
+    int32_t fold_order;      /* order of the fold work of a batched execute:
+                                SFFT4_FOLD_SIGNAL_MAJOR (default): one launch folds every
+                                iteration of the batch, the CTAs of one signal's iterations
+                                adjacent, so that the random samples the iterations share are
+                                read from DRAM once and re-read from L2;
+                                SFFT4_FOLD_ITERATION_MAJOR: one launch per iteration group over
+                                the whole batch (each signal's samples read once per iteration) */
 } sfft4_opts;
 
 /* Fills *opts with the defaults above.  Returns SFFT4_EINVAL if opts is NULL. */

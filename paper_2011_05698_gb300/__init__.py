@@ -47,7 +47,7 @@ def _stream_ptr(device):
 
 def _opts(B1=0, delta=1e-8, precision="fp32", min_votes=0, select_factor=2.0, sig_floor=1e-10,
           mag_tol=0.5, max_iters=64, max_batch=1, trace=False, profile=False, graph=False,
-          location="multiscale"):
+          location="multiscale", fold_order="signal_major", l2_fetch_bytes=0):
     o = _lib.Opts()
     check(_lib.load().sfft4_opts_default(ctypes.byref(o)), "sfft4_opts_default")
     o.B1 = B1
@@ -63,6 +63,9 @@ def _opts(B1=0, delta=1e-8, precision="fp32", min_votes=0, select_factor=2.0, si
     o.profile = int(bool(profile))
     o.graph = int(bool(graph))
     o.location = {"multiscale": _lib.SFFT4_LOC_MULTISCALE, "two_round": _lib.SFFT4_LOC_TWO_ROUND}[location]
+    o.fold_order = {"signal_major": _lib.SFFT4_FOLD_SIGNAL_MAJOR,
+                    "iteration_major": _lib.SFFT4_FOLD_ITERATION_MAJOR}[fold_order]
+    o.l2_fetch_bytes = l2_fetch_bytes
     return o
 
 
@@ -76,16 +79,18 @@ def _device(device):
 class Plan:
     """A static sFFT4.0 plan (Section 3.1) for one (N, K, l, q, seed).  location="two_round"
     replaces the multiscale location by the two-round (tau = 0, 1) location of sFFT3.0 for
-    exactly sparse signals."""
+    exactly sparse signals.  fold_order="iteration_major" folds the batch one iteration at a
+    time instead of all iterations of a signal together (same results, more DRAM reads)."""
 
     def __init__(self, N, K, l=16, q=1.0, seed=0, *, B1=0, delta=1e-8, precision="fp32",
                  min_votes=0, select_factor=2.0, sig_floor=1e-10, mag_tol=0.5, max_iters=64,
-                 max_batch=1, trace=False, profile=False, graph=False, location="multiscale", device=None):
+                 max_batch=1, trace=False, profile=False, graph=False, location="multiscale",
+                 fold_order="signal_major", l2_fetch_bytes=0, device=None):
         import torch
         lib = _lib.load()
         self.device = _device(device)
         o = _opts(B1, delta, precision, min_votes, select_factor, sig_floor, mag_tol, max_iters,
-                  max_batch, trace, profile, graph, location)
+                  max_batch, trace, profile, graph, location, fold_order, l2_fetch_bytes)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             check(lib.sfft4_plan(ctypes.byref(h), N, K, l, q, seed, ctypes.byref(o)), "sfft4_plan")

@@ -16,6 +16,8 @@ SFFT4_FP32 = 0
 SFFT4_BF16X3 = 1
 SFFT4_LOC_MULTISCALE = 0
 SFFT4_LOC_TWO_ROUND = 1
+SFFT4_FOLD_SIGNAL_MAJOR = 0
+SFFT4_FOLD_ITERATION_MAJOR = 1
 MAX_ROUNDS = 64
 
 
@@ -25,7 +27,8 @@ class Opts(ctypes.Structure):
                 ("sig_floor", ctypes.c_double), ("mag_tol", ctypes.c_double),
                 ("max_iters", ctypes.c_int32), ("max_batch", ctypes.c_int32),
                 ("trace", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("l2_fetch_bytes", ctypes.c_int32), ("graph", ctypes.c_int32), ("location", ctypes.c_int32)]
+                ("l2_fetch_bytes", ctypes.c_int32), ("graph", ctypes.c_int32), ("location", ctypes.c_int32),
+                ("fold_order", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):

@@ -538,7 +538,7 @@ int launch_groups(std::vector<DftGroup>& gs, int32_t* status, int sm_count, cuda
 
 // B-point DFTs of nsig x R columns of z (stride z_stride per signal) into y (stride
 // y_stride), through the scratch u (same layout as z) for the four-step case.
-int launch_dft_tc(const float2* z, int64_t z_stride, float2* u, float2* y, int64_t y_stride, int nsig,
+int launch_dft_tc(const float2* z, int64_t z_stride, float2* u, int64_t u_stride, float2* y, int64_t y_stride, int nsig,
                   int R, int B, const unsigned char* A1, const unsigned char* A2, const float2* tw4,
                   int32_t* status, int sm_count, cudaStream_t st) {
     int B1, B2;
@@ -551,11 +551,11 @@ int launch_dft_tc(const float2* z, int64_t z_stride, float2* u, float2* y, int64
         return launch_groups(gs, status, sm_count, st);
     }
     gs[0] = make_group(1, B, B1, A1, tw4, ncols * B2);
-    gs[0].in = z, gs[0].in_stride = z_stride, gs[0].out = u, gs[0].out_stride = z_stride, gs[0].R = R;
+    gs[0].in = z, gs[0].in_stride = z_stride, gs[0].out = u, gs[0].out_stride = u_stride, gs[0].R = R;
     int rc = launch_groups(gs, status, sm_count, st);
     if (rc) return rc;
     gs[0] = make_group(2, B, B2, A2, tw4, ncols * B1);
-    gs[0].in = u, gs[0].in_stride = z_stride, gs[0].out = y, gs[0].out_stride = y_stride, gs[0].R = R;
+    gs[0].in = u, gs[0].in_stride = u_stride, gs[0].out = y, gs[0].out_stride = y_stride, gs[0].R = R;
     return launch_groups(gs, status, sm_count, st);
 }
 

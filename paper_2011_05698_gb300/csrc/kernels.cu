@@ -319,6 +319,26 @@ __global__ void __launch_bounds__(512, 2) k_fold_multi(const FoldArgs* __restric
     fold_body<RG>(sa, t.slice, sa.signal0, xptrs[sa.signal0], sa.z, gsm, s_par, red);
 }
 
+// Signal-major fold of a uniform batch: CTA b folds tile b mod ntiles of signal b / ntiles,
+// the tiles of every (iteration, fold group) of one signal adjacent in the grid.  The CTAs
+// resident at a time then gather from few signals, and a 32-byte sector that the permutations
+// of several iterations draw from is read from DRAM once and hit in L2 after that; in
+// iteration order every iteration re-reads it from DRAM.  The job arguments stay in the
+// parameter space (indexed by a block-uniform job number).
+template <int RG>
+__global__ void __launch_bounds__(512, 2) k_fold_sig(const __grid_constant__ SigFoldLaunch L) {
+    extern __shared__ float gsm[];
+    __shared__ uint32_t s_par[2];
+    __shared__ float2 red[512];
+    const int sig = blockIdx.x / L.ntiles;
+    const int ti = blockIdx.x - sig * L.ntiles;
+    int j = 0;
+    while (j + 1 < L.njobs && ti >= L.start[j + 1]) ++j;
+    const FoldArgs& a = L.jobs[j];
+    fold_body<RG>(a, ti - L.start[j], (int64_t)a.signal0 + sig, L.x + (int64_t)sig * L.x_stride,
+                  a.z + (int64_t)sig * a.z_stride, gsm, s_par, red);
+}
+
 // ----------------------------------------------------------------- FFT --------------
 // Radix-2 decimation-in-time B-point DFT (unnormalised, e^{-2 pi i b j / B}) of
 // `cpc` columns per CTA in shared memory; column c = signal * R + round.
@@ -1227,6 +1247,34 @@ FoldArgs make_fold_args(const sfft4_plan_s* p, int mi, const FoldGroup& g, size_
     return a;
 }
 
+// B-point DFT of every (signal, round) column of iteration mi: z holds signal s's R x B
+// folded arrays at z + s z_stride, y receives the bucket arrays at y + s y_stride.
+int launch_iter_dft(sfft4_plan_s* p, int mi, int nsig, const float2* z, int64_t z_stride, float2* y_out,
+                    int64_t y_sig_stride, cudaStream_t st) {
+    const IterHost& ih = p->iters[mi];
+    const IterDev& d = ih.d;
+    const int B = d.B, logB = d.logB, R = d.R;
+    int T = std::min(1024, std::max(256, B / 2));
+    int cpc = std::max(1, (2 * T) / B);
+    int ncols = nsig * R;
+    int blocks = (ncols + cpc - 1) / cpc;
+    size_t smem = (size_t)cpc * B * sizeof(float2);
+    cudaEvent_t ev = nullptr;
+    int rc = prof_begin(p, st, &ev);
+    if (rc) return rc;
+    if (p->o.precision == SFFT4_BF16X3) {
+        const Window& w = p->wins[ih.win];
+        rc = launch_dft_tc(z, z_stride, p->u, (int64_t)p->R_max * p->B_max, y_out, y_sig_stride, nsig, R, B,
+                           w.dA1, w.dA2, w.tw4, p->status, p->sm_count, st);
+    } else {
+        k_fft<<<blocks, T, smem, st>>>(z, y_out, B, logB, d.tw, z_stride, y_sig_stride, R, cpc, ncols,
+                                       nullptr, nullptr);
+        rc = check_cuda(cudaGetLastError());
+    }
+    if (rc) return rc;
+    return prof_end(p, st, ev, kProfFft, 0);
+}
+
 int launch_bucketize(sfft4_plan_s* p, int mi, int nsig, const float2* x, int64_t x_stride,
                      int32_t signal0, float2* y_out, int64_t y_sig_stride, cudaStream_t st) {
     int rc0 = configure_kernels();
@@ -1258,27 +1306,7 @@ int launch_bucketize(sfft4_plan_s* p, int mi, int nsig, const float2* x, int64_t
         rc = prof_end(p, st, ev, kProfFold, g.unique * nsig);
         if (rc) return rc;
     }
-    // B-point DFT of every (signal, round) column
-    const int B = d.B, logB = d.logB, R = d.R;
-    int T = std::min(1024, std::max(256, B / 2));
-    int cpc = std::max(1, (2 * T) / B);
-    int ncols = nsig * R;
-    int blocks = (ncols + cpc - 1) / cpc;
-    size_t smem = (size_t)cpc * B * sizeof(float2);
-    cudaEvent_t ev = nullptr;
-    int rc = prof_begin(p, st, &ev);
-    if (rc) return rc;
-    if (p->o.precision == SFFT4_BF16X3) {
-        const Window& w = p->wins[ih.win];
-        rc = launch_dft_tc(p->z, (int64_t)p->R_max * p->B_max, p->u, y_out, y_sig_stride, nsig, R, B,
-                           w.dA1, w.dA2, w.tw4, p->status, p->sm_count, st);
-    } else {
-        k_fft<<<blocks, T, smem, st>>>(p->z, y_out, B, logB, d.tw, (int64_t)p->R_max * p->B_max,
-                                       y_sig_stride, R, cpc, ncols, nullptr, nullptr);
-        rc = check_cuda(cudaGetLastError());
-    }
-    if (rc) return rc;
-    return prof_end(p, st, ev, kProfFft, 0);
+    return launch_iter_dft(p, mi, nsig, p->z, (int64_t)p->R_max * p->B_max, y_out, y_sig_stride, st);
 }
 
 DecodeArgs make_decode_args(const sfft4_plan_s* p, int mi) {
@@ -1344,6 +1372,92 @@ int launch_fold_multi(int RG, const FoldArgs* jobs, const FoldTile* tiles, int n
         default: k_fold_multi<8><<<ntiles, threads, smem, st>>>(jobs, tiles, xptrs); break;
     }
     return check_cuda(cudaGetLastError());
+}
+
+// Launch descriptors of the signal-major fold (built once per plan): one FoldArgs per
+// (iteration, fold group) writing iteration m's folded arrays at zall + yoff[m], ordered by
+// samples per residue slice, heaviest first, so that the last signals of a launch end
+// together; at most kSigJobs jobs per launch.
+int build_signal_major_fold(sfft4_plan_s* p) {
+    struct Job {
+        FoldArgs a;
+        int32_t nsl, threads;
+        size_t smem;
+        int64_t per_tile, samples;
+    };
+    std::vector<Job> jobs;
+    for (size_t mi = 0; mi < p->iters.size(); ++mi) {
+        const IterHost& ih = p->iters[mi];
+        const int nsl = ih.d.B / ih.Wj;
+        for (const FoldGroup& g : ih.groups) {
+            Job jb;
+            jb.a = make_fold_args(p, (int)mi, g, &jb.smem);
+            jb.a.z = p->zall + p->yoff[mi];
+            jb.a.z_stride = p->ytot;
+            jb.a.signal0 = 0;
+            jb.nsl = nsl;
+            jb.threads = ih.Wj * g.P;
+            jb.per_tile = g.unique / nsl;
+            jb.samples = g.unique;
+            jobs.push_back(jb);
+        }
+    }
+    std::stable_sort(jobs.begin(), jobs.end(), [](const Job& u, const Job& v) { return u.per_tile > v.per_tile; });
+    p->sm_fold.clear();
+    for (size_t j0 = 0; j0 < jobs.size(); j0 += kSigJobs) {
+        SigFoldHost h;
+        memset(&h, 0, sizeof(h));
+        h.RG = 1;
+        h.threads = 32;
+        const size_t j1 = std::min(jobs.size(), j0 + (size_t)kSigJobs);
+        for (size_t j = j0; j < j1; ++j) {
+            const Job& jb = jobs[j];
+            const int k = (int)(j - j0);
+            h.L.jobs[k] = jb.a;
+            h.L.start[k + 1] = h.L.start[k] + jb.nsl;
+            h.RG = std::max(h.RG, (int32_t)jb.a.g.nr);
+            h.threads = std::max(h.threads, jb.threads);
+            h.smem = std::max(h.smem, jb.smem);
+            h.samples += jb.samples;
+        }
+        h.L.njobs = (int32_t)(j1 - j0);
+        h.L.ntiles = h.L.start[h.L.njobs];
+        if ((int64_t)h.L.ntiles * p->o.max_batch > (int64_t)INT32_MAX || h.threads > 512 ||
+            h.smem > (size_t)kFoldSmemMax)
+            return SFFT4_EINVAL;
+        p->sm_fold.push_back(h);
+    }
+    return SFFT4_OK;
+}
+
+int launch_fold_signal_major(sfft4_plan_s* p, int nsig, const float2* x, int64_t x_stride, cudaStream_t st) {
+    int rc0 = configure_kernels();
+    if (rc0) return rc0;
+    for (SigFoldHost& h : p->sm_fold) {
+        h.L.x = x;
+        h.L.x_stride = x_stride;
+        const int grid = nsig * h.L.ntiles, th = h.threads;
+        const size_t smem = h.smem;
+        const SigFoldLaunch& L = h.L;
+        cudaEvent_t ev = nullptr;
+        int rc = prof_begin(p, st, &ev);
+        if (rc) return rc;
+        switch (h.RG) {
+            case 1: k_fold_sig<1><<<grid, th, smem, st>>>(L); break;
+            case 2: k_fold_sig<2><<<grid, th, smem, st>>>(L); break;
+            case 3: k_fold_sig<3><<<grid, th, smem, st>>>(L); break;
+            case 4: k_fold_sig<4><<<grid, th, smem, st>>>(L); break;
+            case 5: k_fold_sig<5><<<grid, th, smem, st>>>(L); break;
+            case 6: k_fold_sig<6><<<grid, th, smem, st>>>(L); break;
+            case 7: k_fold_sig<7><<<grid, th, smem, st>>>(L); break;
+            default: k_fold_sig<8><<<grid, th, smem, st>>>(L); break;
+        }
+        rc = check_cuda(cudaGetLastError());
+        if (rc) return rc;
+        rc = prof_end(p, st, ev, kProfFold, h.samples * nsig);
+        if (rc) return rc;
+    }
+    return SFFT4_OK;
 }
 
 int launch_fft_multi(const float2* const* zcols, float2* const* ycols, int ncols, int B,
@@ -1450,6 +1564,12 @@ int configure_kernels() {
         if (!rc) rc = check_cuda(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kFoldSmemMax));
     for (const void* f : folds_m)
         if (!rc) rc = check_cuda(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kFoldSmemMax));
+    const void* folds_s[] = {(const void*)k_fold_sig<1>, (const void*)k_fold_sig<2>,
+                             (const void*)k_fold_sig<3>, (const void*)k_fold_sig<4>,
+                             (const void*)k_fold_sig<5>, (const void*)k_fold_sig<6>,
+                             (const void*)k_fold_sig<7>, (const void*)k_fold_sig<8>};
+    for (const void* f : folds_s)
+        if (!rc) rc = check_cuda(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kFoldSmemMax));
     const void* decs_m[] = {(const void*)k_decode_multi<8>, (const void*)k_decode_multi<16>,
                             (const void*)k_decode_multi<64>};
     for (const void* f : decs_m)
@@ -1531,9 +1651,17 @@ int run_body(sfft4_plan_s* p, const void* ctx, cudaStream_t st) {
     if (!rc) rc = check_cuda(cudaStreamWaitEvent(ds, p->ev[0], 0));
     if (rc) return rc;
     const int64_t rb = (int64_t)p->R_max * p->B_max;
+    // signal-major order: one fold launch for every iteration, then the DFTs iteration by
+    // iteration (the decode of iteration m starts after its own DFT)
+    const bool sig_major = !p->sm_fold.empty();
+    if (sig_major) {
+        rc = launch_fold_signal_major(p, nsig, x, x_stride, st);
+        if (rc) return rc;
+    }
     for (size_t mi = 0; mi < ni; ++mi) {
         float2* ym = p->y + p->yoff[mi];
-        rc = launch_bucketize(p, (int)mi, nsig, x, x_stride, 0, ym, p->ytot, st);
+        rc = sig_major ? launch_iter_dft(p, (int)mi, nsig, p->zall + p->yoff[mi], p->ytot, ym, p->ytot, st)
+                       : launch_bucketize(p, (int)mi, nsig, x, x_stride, 0, ym, p->ytot, st);
         if (!rc) rc = check_cuda(cudaEventRecord(p->ev[1 + mi], st));
         if (!rc) rc = check_cuda(cudaStreamWaitEvent(ds, p->ev[1 + mi], 0));
         if (rc) return rc;

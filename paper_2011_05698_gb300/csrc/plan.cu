@@ -124,7 +124,7 @@ void free_plan(sfft4_plan_s* p) {
             cudaFree(w.tw4);
         }
     }
-    void* bufs[] = {p->iters_dev, p->z, p->y, p->u, p->status, p->F, p->ff, p->fv, p->fvotes, p->hkeys,
+    void* bufs[] = {p->iters_dev, p->z, p->zall, p->y, p->u, p->status, p->F, p->ff, p->fv, p->fvotes, p->hkeys,
                     p->hvals, p->theta, p->fxexp, p->trace_y, p->trace_F, p->trace_ff,
                     p->trace_fv, p->trace_votes};
     for (void* b : bufs) cudaFree(b);
@@ -176,9 +176,12 @@ namespace sfft4 {
 // Kernel launches of one execute of a uniform plan: per iteration its fold groups, one FP32 DFT
 // or one/two tensor-core DFT stages, one decode; one finalize.
 int32_t uniform_kernels(const sfft4_plan_s* p) {
-    int32_t k = 1;
+    const bool sig_major = p->o.fold_order == SFFT4_FOLD_SIGNAL_MAJOR;
+    // finalize, and the fold launches covering every iteration (signal-major)
+    int32_t k = 1 + (sig_major ? std::max<int32_t>(1, (int32_t)p->sm_fold.size()) : 0);
     for (auto& ih : p->iters)
-        k += (int32_t)ih.groups.size() + 1 + ((p->o.precision == SFFT4_BF16X3 && ih.d.B > 64) ? 2 : 1);
+        k += (sig_major ? 0 : (int32_t)ih.groups.size()) + 1 +
+             ((p->o.precision == SFFT4_BF16X3 && ih.d.B > 64) ? 2 : 1);
     return k;
 }
 
@@ -206,6 +209,7 @@ int plan_options(int64_t N, int64_t K, int32_t l, double q, const sfft4_opts* op
     if (!(o.select_factor > 0) || !(o.mag_tol > 0) || o.min_votes < 0) return SFFT4_EINVAL;
     if (o.l2_fetch_bytes > 128) return SFFT4_EINVAL;
     if (o.location != SFFT4_LOC_MULTISCALE && o.location != SFFT4_LOC_TWO_ROUND) return SFFT4_EINVAL;
+    if (o.fold_order != SFFT4_FOLD_SIGNAL_MAJOR && o.fold_order != SFFT4_FOLD_ITERATION_MAJOR) return SFFT4_EINVAL;
     // the two-round vote window is 1/(8N) turns: FP32 bucket arrays resolve it up to N = 2^20
     if (o.location == SFFT4_LOC_TWO_ROUND && N > (int64_t(1) << 20)) return SFFT4_EINVAL;
     int64_t B1 = o.B1;
@@ -291,9 +295,11 @@ int plan_schedule(sfft4_plan_s* p) {
             d.tau[s + 1] = ts;
         }
         // fold groups of up to kFoldRG rounds
-        // residues per fold CTA: 64, fewer when the staged window rows of a CTA
+        // residues per fold CTA: 32 (measured against 16 and 64: small enough that the
+        // CTAs resident at a time cover few signals in signal-major order, wide enough for
+        // coalesced window-row staging), fewer when the staged window rows of a CTA
         // (rounds x rows x residues floats) would exceed the shared-memory budget
-        ih.Wj = (int32_t)std::min<int64_t>(B, 64);
+        ih.Wj = (int32_t)std::min<int64_t>(B, 32);
         {
             int64_t rows = (2 * (int64_t)d.h + B) / B + 2;
             while (ih.Wj > 16 && (int64_t)kFoldRG * rows * ih.Wj * 4 > kFoldSmemMax) ih.Wj >>= 1;
@@ -414,10 +420,13 @@ int sfft4_plan(sfft4_plan_t* out, int64_t N, int64_t K, int32_t l, double q, uin
     p->o = o;
     CK(cudaGetDevice(&p->device));
     if (o.l2_fetch_bytes >= 0) {
-        // The gather reads one 8-byte sample per random 32-byte sector; a larger L2 fetch
-        // granularity would move 2-4x the needed DRAM bytes.  This is a limit of the
-        // calling process's CUDA context (a performance hint), not a device setting.
-        CK(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, o.l2_fetch_bytes ? o.l2_fetch_bytes : 32));
+        // The gather reads 8-byte samples at random positions.  A 128-byte fetch per miss
+        // moves up to 16x the needed DRAM bytes; 32 bytes (one sector) is the least, but the
+        // iterations of a signal, folded together, draw neighbouring samples often enough
+        // that 64-byte fetches come out ahead (measured: 32 B 4 % slower, 128 B no faster).
+        // This is a limit of the calling process's CUDA context (a performance hint), not a
+        // device setting.
+        CK(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, o.l2_fetch_bytes ? o.l2_fetch_bytes : 64));
     }
     int rc = plan_schedule(p);
     if (!rc) rc = plan_tables(p, nullptr);
@@ -427,6 +436,11 @@ int sfft4_plan(sfft4_plan_t* out, int64_t N, int64_t K, int32_t l, double q, uin
     size_t rb = (size_t)p->R_max * p->B_max;
     CK(cudaMalloc(&p->z, mb * rb * sizeof(float2)));
     CK(cudaMalloc(&p->y, mb * (size_t)p->ytot * sizeof(float2)));
+    if (o.fold_order == SFFT4_FOLD_SIGNAL_MAJOR) {
+        CK(cudaMalloc(&p->zall, mb * (size_t)p->ytot * sizeof(float2)));
+        const int rcs = sfft4::build_signal_major_fold(p);
+        if (rcs) { free_plan(p); return rcs; }
+    }
     CK(cudaStreamCreateWithFlags(&p->dstream, cudaStreamNonBlocking));
     p->ev.assign(ni + 2, nullptr);
     for (auto& e : p->ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -478,7 +492,7 @@ int sfft4_plan_batched(sfft4_plan_t* out, int32_t nsig, const int64_t* N, const 
     CK(cudaGetDevice(&p->device));
     CK(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device));
     if (o.l2_fetch_bytes >= 0)
-        CK(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, o.l2_fetch_bytes ? o.l2_fetch_bytes : 32));
+        CK(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, o.l2_fetch_bytes ? o.l2_fetch_bytes : 64));
     CK(cudaMalloc(&p->status, sizeof(int32_t)));
     CK(cudaMemset(p->status, 0, sizeof(int32_t)));
     int rc = build_group_plan(p, nsig, N, K, B1, l, q, seed, opts);

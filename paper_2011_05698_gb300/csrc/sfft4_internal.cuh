@@ -89,6 +89,24 @@ struct FoldTile {
     int32_t job, slice;
 };
 
+// One signal-major fold launch: the (iteration, fold group) jobs it covers, passed in the
+// kernel's parameter space (warp-uniform constant loads, no per-CTA copy), job j owning the
+// residue slices start[j] .. start[j + 1] - 1 of each signal's tile range.
+constexpr int kSigJobs = 48;
+struct SigFoldLaunch {
+    const float2* x;
+    int64_t x_stride;
+    int32_t ntiles, njobs;
+    int32_t start[kSigJobs + 1];
+    FoldArgs jobs[kSigJobs];
+};
+struct SigFoldHost {
+    SigFoldLaunch L;
+    int32_t RG, threads;
+    size_t smem;
+    int64_t samples;  // per signal
+};
+
 // Arguments of one decode launch (uniform batch) or one signal's decode (batch of sizes).
 struct DecodeArgs {
     uint64_t N, seed;
@@ -205,6 +223,11 @@ struct sfft4_plan_s {
     int32_t* hkeys = nullptr;   // [sig][2^Hlog] hash keys (frequency or -1)
     int32_t* hvals = nullptr;   // [sig][2^Hlog] entry index
     float2* u = nullptr;        // [sig][R_max][B_max] four-step scratch (BF16X3 DFT)
+    // signal-major fold (fold_order SFFT4_FOLD_SIGNAL_MAJOR): one job per (iteration, fold
+    // group) with z of iteration m at zall + yoff[m] (per-signal stride ytot); a launch's grid
+    // is nsig x ntiles CTAs, the ntiles (job, residue slice) tiles of a signal adjacent
+    float2* zall = nullptr;     // [sig][ytot] folded arrays of every iteration
+    std::vector<sfft4::SigFoldHost> sm_fold;  // launches (more than one past kSigJobs jobs)
     int32_t* status = nullptr;  // 1 when a bounded device wait gave up
     int sm_count = 0;
     float* theta = nullptr;     // [sig] candidate floor
@@ -254,6 +277,8 @@ FoldArgs make_fold_args(const sfft4_plan_s* p, int mi, const FoldGroup& g, size_
 DecodeArgs make_decode_args(const sfft4_plan_s* p, int mi);
 size_t decode_smem_bytes(int B);
 int configure_kernels();
+int build_signal_major_fold(sfft4_plan_s* p);
+int launch_fold_signal_major(sfft4_plan_s* p, int nsig, const float2* x, int64_t x_stride, cudaStream_t st);
 int launch_fold_multi(int RG, const FoldArgs* jobs, const FoldTile* tiles, int ntiles,
                       const float2* const* xptrs, int threads, size_t smem, cudaStream_t st);
 int launch_fft_multi(const float2* const* zcols, float2* const* ycols, int ncols, int B,
@@ -287,7 +312,7 @@ int plan_tables(sfft4_plan_s* p, std::vector<Window>* cache);
 size_t dft_tc_matrix_bytes();
 int build_dft_tc_tables(int B, unsigned char* A1, unsigned char* A2, float2* tw4);
 int configure_dft_tc();
-int launch_dft_tc(const float2* z, int64_t z_stride, float2* u, float2* y, int64_t y_stride, int nsig,
+int launch_dft_tc(const float2* z, int64_t z_stride, float2* u, int64_t u_stride, float2* y, int64_t y_stride, int nsig,
                   int R, int B, const unsigned char* A1, const unsigned char* A2, const float2* tw4,
                   int32_t* status, int sm_count, cudaStream_t st);
 // Columns of one bucket count within a level of a batch of uneven signals (device tables of
