@@ -44,19 +44,25 @@ __device__ __forceinline__ float2 cis_2pi_frac(uint64_t r, int n) {
     return make_float2(ca * cb - sa * sb, sa * cb + ca * sb);
 }
 
-// rint(x) as int64 (round half to even, as __float2ll_rn) with 32-bit conversions: for
-// |x| < 2^47, x = h 2^24 + d with h = rint(x / 2^24) and d exact (one fmaf), and
-// rint(x) = h 2^24 + rint(d) because h 2^24 is an even integer.
+// rint(x) as int64 (round half to even, as __float2ll_rn) in float adds: for |x| <= 2^45,
+// x = h 2^23 + d with h = rint(x / 2^23) and d exact (one fmaf, |d| <= 2^22), and
+// rint(x) = h 2^23 + rint(d) because h 2^23 is an even integer.  Both roundings add
+// 1.5 2^23: a float in [2^23, 2^24] has unit spacing, so the sum is rounded to the nearest
+// integer (half to even) and its low mantissa bits hold that integer plus 2^22.  This keeps
+// the float-to-int conversion unit (a few lanes per clock) out of the update's inner loop.
 // Out-of-range cases call the 64-bit conversion in a separate function, so that the
 // compiler cannot if-convert it into every lane.
 __device__ __noinline__ long long f2ll_rn_wide(float x) { return __float2ll_rn(x); }
 __device__ __noinline__ float ll2f_rn_wide(long long v) { return __ll2float_rn(v); }
 
 __device__ __forceinline__ long long f2ll_rn(float x) {
-    if (!(fabsf(x) < 0x1p47f)) return f2ll_rn_wide(x);
-    const int h = __float2int_rn(x * 0x1p-24f);
-    const float d = fmaf(-(float)h, 0x1p24f, x);
-    return ((long long)h << 24) + __float2int_rn(d);
+    if (!(fabsf(x) <= 0x1p45f)) return f2ll_rn_wide(x);
+    constexpr float M = 12582912.f;  // 1.5 2^23
+    const float th = __fadd_rn(x * 0x1p-23f, M);
+    const int h = __float_as_int(th) - 0x4B400000;
+    const float d = fmaf(-__fsub_rn(th, M), 0x1p23f, x);
+    const int r = __float_as_int(__fadd_rn(d, M)) - 0x4B400000;
+    return ((long long)h << 23) + r;
 }
 
 // The float nearest to v (ties to even, as __ll2float_rn): for |v| < 2^48, v = h 2^24 + l
@@ -718,11 +724,17 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig) 
             __syncthreads();
             for (int r0 = 0; r0 < R; r0 += kUpdRounds) {
                 const int nr = min(kUpdRounds, R - r0);
-                for (int i = tid; i < F0 * kUpdRounds; i += T) {
-                    const int pos = i / kUpdRounds, rr = i - pos * kUpdRounds;
-                    if (rr < nr) {
-                        const uint32_t o_r = (aoff + sigma * (uint32_t)it->tau[r0 + rr]) & mask;
-                        ec[i] = cmul(ev[pos], cis_2pi_frac((ef[pos] * o_r) & mask, n));
+                // round-major (ec[rr F0 + j]): the entries a warp gathers below fall in
+                // different banks (entry-major rows of 32 bytes would share 4 bank positions)
+                for (int pos = tid; pos < F0; pos += T) {
+                    const float2 v = ev[pos];
+                    const uint32_t f = ef[pos];
+#pragma unroll
+                    for (int rr = 0; rr < kUpdRounds; ++rr) {
+                        if (rr < nr) {
+                            const uint32_t o_r = (aoff + sigma * (uint32_t)it->tau[r0 + rr]) & mask;
+                            ec[rr * F0 + pos] = cmul(v, cis_2pi_frac((f * o_r) & mask, n));
+                        }
                     }
                 }
                 __syncthreads();
@@ -741,7 +753,7 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig) 
 #pragma unroll
                             for (int rr = 0; rr < kUpdRounds; ++rr) {
                                 if (rr < nr) {
-                                    const float2 c = ec[j * kUpdRounds + rr];
+                                    const float2 c = ec[rr * F0 + j];
                                     ar[rr] += f2ll_rn(g * c.x);
                                     ai[rr] += f2ll_rn(g * c.y);
                                 }

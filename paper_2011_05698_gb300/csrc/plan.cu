@@ -306,9 +306,12 @@ int plan_schedule(sfft4_plan_s* p) {
             if ((int64_t)kFoldRG * rows * ih.Wj * 4 > kFoldSmemMax) return SFFT4_EINVAL;
         }
         ih.unique = 0;
-        for (int r0 = 0; r0 < d.R; r0 += kFoldRG) {
+        // balanced groups of at most kFoldGroupMax rounds (the fold kernel's accumulator count
+        // is the largest group of its launch)
+        const int ngr = (d.R + kFoldGroupMax - 1) / kFoldGroupMax, gsz = (d.R + ngr - 1) / ngr;
+        for (int r0 = 0; r0 < d.R; r0 += gsz) {
             FoldGroup g;
-            build_group(&g, d.tau, r0, std::min(kFoldRG, d.R - r0), d.h);
+            build_group(&g, d.tau, r0, std::min(gsz, d.R - r0), d.h);
             int64_t per = (g.unique + B * 12 - 1) / (B * 12);
             g.P = (int32_t)std::max<int64_t>(1, std::min<int64_t>(512 / ih.Wj, per));
             ih.groups.push_back(g);

@@ -14,6 +14,8 @@ namespace sfft4 {
 
 constexpr int kMaxRounds = SFFT4_MAX_ROUNDS;  // R = S + 1 <= 64 rounds per iteration
 constexpr int kFoldRG = 8;                    // rounds accumulated per fold launch group
+constexpr int kFoldGroupMax = 6;              // rounds per fold group the planner forms (measured
+                                              // against 5 and 8 on N = 2^22, K = 1000)
 constexpr int kMaxSeg = 2 * kFoldRG + 2;      // t-segments of one fold group
 constexpr int kQDen = 256;                    // q = q_n / 256
 constexpr int kBMin = 16;
