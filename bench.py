@@ -454,7 +454,9 @@ def rank_seed0(rank):
     return 1_000_000 * (rank + 1)
 
 
-def timed(fn, steps, warmup, stream, dist=None):
+def timed(fn, steps, warmup, stream, dist=None, finish=None):
+    """Seconds of `steps` calls of fn between CUDA events on `stream` (finish() is issued
+    after the last call, before the closing event: it joins work fn left on other streams)."""
     import torch
     for _ in range(warmup):
         fn()
@@ -466,6 +468,8 @@ def timed(fn, steps, warmup, stream, dist=None):
     e0.record(stream)
     for _ in range(steps):
         fn()
+    if finish is not None:
+        finish()
     e1.record(stream)
     torch.cuda.synchronize()
     if dist is not None:
@@ -490,6 +494,8 @@ def main():
     ap.add_argument("--no-fp32-form", action="store_true")
     ap.add_argument("--fold-order", default="signal_major", choices=["signal_major", "iteration_major"],
                     help="fold order of the headline plan")
+    ap.add_argument("--no-async", action="store_true",
+                    help="headline steps as synchronous executes (no overlap between batches)")
     ap.add_argument("--form", default="all", choices=["all", "uneven", "sweep", "configs", "phase_error"],
                     help="uneven: time only the uneven-batch form; sweep: the large-N SNR x (l, q) "
                          "sweep (N = 2^26, K = 4000, 10 seeds)")
@@ -553,21 +559,40 @@ def main():
                    precision=args.precision, fold_order=args.fold_order)
     xs = device_batch(N_DEF, K_DEF, S, rank_seed0(rank), args.snr, dev)
     out = plan._outputs(S)
+    outs = [out, plan._outputs(S)]
     stream = torch.cuda.current_stream(dev)
+    pipelined = not args.no_async
+    counter = [0]
 
     def step():
-        plan.execute_batched(xs, out)
+        # one batch per step; pipelined: asynchronous executes (two workspaces in turn), so
+        # the decode chain of one batch overlaps the gather of the next
+        if pipelined:
+            plan.execute_batched(xs, outs[counter[0] % 2], asynchronous=True)
+            counter[0] += 1
+        else:
+            plan.execute_batched(xs, out)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     plan.profile(reset=True)
     with ClockSampler(local) as clk:
-        el = timed(step, args.steps, 0, stream, dist)
+        el = timed(step, args.steps, 0, stream, dist, finish=plan.wait if pipelined else None)
     prof = plan.profile(reset=True)
     el = max_over_ranks(el, dist, dev)
     value = S * args.steps * world / el
     ms_per_step = 1e3 * el / args.steps
+    # the same batches one synchronous execute at a time (each step's results complete on
+    # the caller's stream before the next starts)
+    sync_form = None
+    if pipelined:
+        ksync = max(3, min(args.steps, 30))
+        el_s = timed(lambda: plan.execute_batched(xs, out), ksync, 2, stream, dist)
+        el_s = max_over_ranks(el_s, dist, dev)
+        sync_form = {"value": S * ksync * world / el_s, "ms_per_step": 1e3 * el_s / ksync,
+                     "form": "one synchronous execute per step"}
+        plan.profile(reset=True)
 
     # dominant kernel: the permuted gather + window + fold
     peak, peak_kind = measured_peaks()
@@ -737,13 +762,17 @@ def main():
                            "snr_db": args.snr, "batch_per_gpu": S, "B1": plan.info["B1"],
                            "iterations": plan.info["n_iters"], "precision": args.precision,
                            "fold_order": args.fold_order,
+                           "execute": ("asynchronous, two workspaces in turn (batch k's decode chain "
+                                       "overlaps batch k+1's gather)") if pipelined else "synchronous",
                            "samples_per_transform": plan.info["samples_per_transform"],
                            "l2": "inputs larger than L2 (touched samples per step "
                                  f"{S * plan.info['samples_per_transform'] * 32 / 1e9:.1f} GB of 32 B sectors)",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": plan.info["kernels_per_execute"] * args.steps,
-                "clocks": clk.summary(), "forms": {"batched": {"value": value, "precision": args.precision},
+                "clocks": clk.summary(), "forms": {"batched": {"value": value, "precision": args.precision,
+                                                               "pipelined": pipelined},
+                                                   "batched_sync": sync_form,
                                                    "batched_fp32": fp32_form, "plain_fp32": plain, "plain_fp32_graph": plain_graph,
                                                    "uneven_batch": uneven, "dense_fft_context": dense}}
         print(json.dumps(line), flush=True)

@@ -156,6 +156,29 @@ SFFT4_API int sfft4_execute_batched(sfft4_plan_t plan, int32_t nsig, const void*
                           int8_t* votes_dev, void* stream);
 
 /*
+ * sfft4_execute_batched_async -- sfft4_execute_batched for a pipeline of batches: the
+ * transforms of one batch (same arguments and results) run on the plan's own streams after
+ * the work queued on `stream` so far, and `stream` does not wait for them, so consecutive
+ * calls overlap (the decode chain of one batch with the gather of the next).  Calls use two
+ * workspaces in turn; the first call allocates the second (a plan of the same transform and
+ * options, created synchronously).  A third call queues behind the first one's work.
+ *   Results are complete once sfft4_wait(plan, s) has been issued on a stream s and s has
+ *   reached that point.  x_dev and the output buffers of a call must stay valid and
+ *   unmodified until then; calls in flight together need distinct output buffers.
+ *   A synchronous execute on the same plan waits for the asynchronous one that used the
+ *   plan's own workspace.
+ * Errors: SFFT4_EINVAL, SFFT4_ESTATE (a plan of sfft4_plan_batched, or opts.trace set),
+ * SFFT4_ENOMEM, SFFT4_ECUDA.
+ */
+SFFT4_API int sfft4_execute_batched_async(sfft4_plan_t plan, int32_t nsig, const void* x_dev, int64_t x_stride,
+                                          int64_t* idx_dev, sfft4_c128* val_dev, int64_t* nfound_dev,
+                                          int8_t* votes_dev, void* stream);
+
+/* Makes `stream` wait for every sfft4_execute_batched_async call issued so far on the plan.
+ * Errors: SFFT4_EINVAL, SFFT4_ECUDA. */
+SFFT4_API int sfft4_wait(sfft4_plan_t plan, void* stream);
+
+/*
  * sfft4_plan_batched -- plan of nsig transforms of different sizes, executed together
  * (batch of independent problems; each signal follows its own static schedule of Section 3.1).
  *   N[i], K[i]  size and sparsity of signal i, each within sfft4_plan's limits

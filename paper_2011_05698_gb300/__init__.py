@@ -191,16 +191,25 @@ class Plan:
                                         _stream_ptr(self.device)), "sfft4_execute")
         return idx[0], val[0], nf[0], votes[0]
 
-    def execute_batched(self, xs, out=None):
-        """Transforms of each row of xs (shape (nsig, N), complex64, on the device)."""
+    def execute_batched(self, xs, out=None, asynchronous=False):
+        """Transforms of each row of xs (shape (nsig, N), complex64, on the device).  With
+        asynchronous=True the batch runs on the plan's own streams and overlaps the next call
+        (two workspaces in turn); its results are complete after wait().  xs and the outputs
+        must then stay untouched until wait(), and calls in flight together need distinct
+        output buffers."""
         self._check_x(xs, 2)
         nsig = xs.shape[0]
         idx, val, nf, votes = out if out is not None else self._outputs(nsig)
-        check(_lib.load().sfft4_execute_batched(self._h, nsig, ctypes.c_void_p(xs.data_ptr()), xs.stride(0),
-                                                ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(val.data_ptr()),
-                                                ctypes.c_void_p(nf.data_ptr()), ctypes.c_void_p(votes.data_ptr()),
-                                                _stream_ptr(self.device)), "sfft4_execute_batched")
+        fn = "sfft4_execute_batched_async" if asynchronous else "sfft4_execute_batched"
+        check(getattr(_lib.load(), fn)(self._h, nsig, ctypes.c_void_p(xs.data_ptr()), xs.stride(0),
+                                       ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(val.data_ptr()),
+                                       ctypes.c_void_p(nf.data_ptr()), ctypes.c_void_p(votes.data_ptr()),
+                                       _stream_ptr(self.device)), fn)
         return idx, val, nf, votes
+
+    def wait(self):
+        """Makes the current stream wait for every asynchronous execute issued so far."""
+        check(_lib.load().sfft4_wait(self._h, _stream_ptr(self.device)), "sfft4_wait")
 
     def bucketize(self, x, m, signal=0):
         """Raw bucket arrays (R, B) of iteration m for Philox signal index `signal` (Lemma 1)."""

@@ -1722,11 +1722,61 @@ int run(sfft4_plan_s* p, int nsig, const float2* x, int64_t x_stride, int64_t* i
 
 extern "C" {
 
+// A synchronous execute uses the plan's own workspace (slot 0 of the asynchronous ones).
+static int join_slot0(sfft4_plan_s* p, cudaStream_t st) {
+    return (p->async_used & 1) ? check_cuda(cudaStreamWaitEvent(st, p->ev_done[0], 0)) : SFFT4_OK;
+}
+
 int sfft4_execute(sfft4_plan_t p, const void* x_dev, int64_t* idx_dev, sfft4_c128* val_dev,
                   int64_t* nfound_dev, int8_t* votes_dev, void* stream) {
     if (!p || !x_dev || !idx_dev || !val_dev || !nfound_dev) return SFFT4_EINVAL;
+    int rc = join_slot0(p, (cudaStream_t)stream);
+    if (rc) return rc;
     return run(p, 1, (const float2*)x_dev, p->N, idx_dev, val_dev, nfound_dev, votes_dev,
                (cudaStream_t)stream);
+}
+
+int sfft4_execute_batched_async(sfft4_plan_t p, int32_t nsig, const void* x_dev, int64_t x_stride,
+                                int64_t* idx_dev, sfft4_c128* val_dev, int64_t* nfound_dev,
+                                int8_t* votes_dev, void* stream) {
+    if (!p || !x_dev || !idx_dev || !val_dev || !nfound_dev) return SFFT4_EINVAL;
+    if (p->grp || p->o.trace) return SFFT4_ESTATE;
+    if (nsig < 1 || nsig > p->o.max_batch || x_stride < p->N) return SFFT4_EINVAL;
+    int rc = SFFT4_OK;
+    if (!p->peer) {
+        // the second workspace: a plan of the same transform and options
+        rc = sfft4_plan(&p->peer, p->N, p->K, p->l, (double)p->qn / kQDen, p->seed, &p->o);
+        if (rc) return rc;
+        for (int s = 0; s < 2 && !rc; ++s) {
+            rc = check_cuda(cudaStreamCreateWithFlags(&p->astream[s], cudaStreamNonBlocking));
+            if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&p->ev_in[s], cudaEventDisableTiming));
+            if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&p->ev_done[s], cudaEventDisableTiming));
+        }
+        if (rc) return rc;
+    }
+    const int s = p->async_next;
+    sfft4_plan_s* w = s ? p->peer : p;
+    cudaStream_t as = p->astream[s];
+    // the execute reads x after the work queued on `stream` so far; slot s's previous execute
+    // is ahead of it on the slot's stream
+    rc = check_cuda(cudaEventRecord(p->ev_in[s], (cudaStream_t)stream));
+    if (!rc) rc = check_cuda(cudaStreamWaitEvent(as, p->ev_in[s], 0));
+    if (!rc) rc = run(w, nsig, (const float2*)x_dev, x_stride, idx_dev, val_dev, nfound_dev, votes_dev, as);
+    if (!rc) rc = check_cuda(cudaEventRecord(p->ev_done[s], as));
+    if (rc) return rc;
+    p->async_used |= 1 << s;
+    p->async_next = s ^ 1;
+    return SFFT4_OK;
+}
+
+int sfft4_wait(sfft4_plan_t p, void* stream) {
+    if (!p) return SFFT4_EINVAL;
+    for (int s = 0; s < 2; ++s)
+        if ((p->async_used >> s) & 1) {
+            const int rc = check_cuda(cudaStreamWaitEvent((cudaStream_t)stream, p->ev_done[s], 0));
+            if (rc) return rc;
+        }
+    return SFFT4_OK;
 }
 
 int sfft4_execute_batched(sfft4_plan_t p, int32_t nsig, const void* x_dev, int64_t x_stride,
@@ -1735,6 +1785,8 @@ int sfft4_execute_batched(sfft4_plan_t p, int32_t nsig, const void* x_dev, int64
     if (!p || !x_dev || !idx_dev || !val_dev || !nfound_dev) return SFFT4_EINVAL;
     if (p->grp) return SFFT4_ESTATE;
     if (nsig < 1 || nsig > p->o.max_batch || x_stride < p->N) return SFFT4_EINVAL;
+    int rc = join_slot0(p, (cudaStream_t)stream);
+    if (rc) return rc;
     return run(p, nsig, (const float2*)x_dev, x_stride, idx_dev, val_dev, nfound_dev, votes_dev,
                (cudaStream_t)stream);
 }
@@ -1751,8 +1803,8 @@ int sfft4_bucketize(sfft4_plan_t p, const void* x_dev, int32_t signal, int32_t m
 int sfft4_stats(sfft4_plan_t p, sfft4_run_stats* out) {
     if (!p || !out) return SFFT4_EINVAL;
     memset(out, 0, sizeof(*out));
-    out->executes = p->n_executes;
-    out->transforms = p->n_transforms;
+    out->executes = p->n_executes + (p->peer ? p->peer->n_executes : 0);
+    out->transforms = p->n_transforms + (p->peer ? p->peer->n_transforms : 0);
     out->last_nsig = p->last_nsig;
     std::vector<FinalJob> jobs;
     if (p->grp) {
@@ -1820,6 +1872,21 @@ int sfft4_sync_status(sfft4_plan_t p) {
 int sfft4_profile_get(sfft4_plan_t p, sfft4_profile* out, int32_t reset) {
     if (!p || !out) return SFFT4_EINVAL;
     if (!p->o.profile) return SFFT4_ESTATE;
+    if (p->peer) {
+        // the second workspace's launches (asynchronous executes) count with this plan's
+        sfft4_profile q;
+        int rc = sfft4_profile_get(p->peer, &q, 1);
+        if (rc) return rc;
+        p->prof_tot.fold_launches += q.fold_launches;
+        p->prof_tot.fold_ms += q.fold_ms;
+        p->prof_tot.fold_samples += q.fold_samples;
+        p->prof_tot.fft_launches += q.fft_launches;
+        p->prof_tot.fft_ms += q.fft_ms;
+        p->prof_tot.decode_launches += q.decode_launches;
+        p->prof_tot.decode_ms += q.decode_ms;
+        p->prof_tot.finalize_launches += q.finalize_launches;
+        p->prof_tot.finalize_ms += q.finalize_ms;
+    }
     for (auto& r : p->prof) {
         int rc = check_cuda(cudaEventSynchronize(r.b));
         if (rc) return rc;

@@ -230,6 +230,13 @@ struct sfft4_plan_s {
     // is nsig x ntiles CTAs, the ntiles (job, residue slice) tiles of a signal adjacent
     float2* zall = nullptr;     // [sig][ytot] folded arrays of every iteration
     std::vector<sfft4::SigFoldHost> sm_fold;  // launches (more than one past kSigJobs jobs)
+    // asynchronous executes (sfft4_execute_batched_async): two workspaces, this plan's and a
+    // peer plan's, used in turn on their own streams; ev_done[s] marks slot s's latest execute
+    sfft4_plan_s* peer = nullptr;
+    cudaStream_t astream[2] = {nullptr, nullptr};
+    cudaEvent_t ev_in[2] = {nullptr, nullptr};
+    cudaEvent_t ev_done[2] = {nullptr, nullptr};
+    int async_next = 0, async_used = 0;
     int32_t* status = nullptr;  // 1 when a bounded device wait gave up
     int sm_count = 0;
     float* theta = nullptr;     // [sig] candidate floor

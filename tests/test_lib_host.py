@@ -121,6 +121,8 @@ def test_execute_rejects_null_arguments(lib):
     assert lib.sfft4_execute_batched_v(None, None, None, None, None, None, None) == _lib.SFFT4_EINVAL
     assert lib.sfft4_get_batch_info(None, None) == _lib.SFFT4_EINVAL
     assert lib.sfft4_stats(None, None) == _lib.SFFT4_EINVAL
+    assert lib.sfft4_execute_batched_async(None, 1, None, 0, None, None, None, None, None) == _lib.SFFT4_EINVAL
+    assert lib.sfft4_wait(None, None) == _lib.SFFT4_EINVAL
     lib.sfft4_destroy(None)
 
 
