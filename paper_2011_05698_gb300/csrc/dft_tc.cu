@@ -559,6 +559,34 @@ int launch_dft_tc(const float2* z, int64_t z_stride, float2* u, int64_t u_stride
     return launch_groups(gs, status, sm_count, st);
 }
 
+// DFTs of every iteration of a uniform batch at once (the signal-major fold has made all
+// their folded arrays): one launch for the single-stage and first four-step stages of every
+// iteration, one for the second stages, instead of one or two launches per iteration.
+int launch_dft_tc_strided(const DftStrided* sets, int nsets, int32_t* status, int sm_count, cudaStream_t st) {
+    std::vector<DftGroup> a, b;
+    for (int i = 0; i < nsets; ++i) {
+        const DftStrided& c = sets[i];
+        int B1, B2;
+        dft_factor(c.B, &B1, &B2);
+        const int64_t ncols = (int64_t)c.nsig * c.R;
+        if (B2 == 1) {
+            DftGroup g = make_group(0, c.B, c.B, c.A1, c.tw4, ncols);
+            g.in = c.z, g.in_stride = c.z_stride, g.out = c.y, g.out_stride = c.y_stride, g.R = c.R;
+            a.push_back(g);
+        } else {
+            DftGroup g1 = make_group(1, c.B, B1, c.A1, c.tw4, ncols * B2);
+            g1.in = c.z, g1.in_stride = c.z_stride, g1.out = c.u, g1.out_stride = c.u_stride, g1.R = c.R;
+            a.push_back(g1);
+            DftGroup g2 = make_group(2, c.B, B2, c.A2, c.tw4, ncols * B1);
+            g2.in = c.u, g2.in_stride = c.u_stride, g2.out = c.y, g2.out_stride = c.y_stride, g2.R = c.R;
+            b.push_back(g2);
+        }
+    }
+    int rc = launch_groups(a, status, sm_count, st);
+    if (!rc) rc = launch_groups(b, status, sm_count, st);
+    return rc;
+}
+
 // DFTs of column sets of several bucket counts (a level of a batch of uneven signals): one
 // launch for the single-stage and first four-step stages of every set, one for the second.
 int launch_dft_tc_sets(const DftColSet* sets, int nsets, int32_t* status, int sm_count, cudaStream_t st) {

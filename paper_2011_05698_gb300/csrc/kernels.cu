@@ -1666,17 +1666,38 @@ int run_body(sfft4_plan_s* p, const void* ctx, cudaStream_t st) {
     // signal-major order: one fold launch for every iteration, then the DFTs iteration by
     // iteration (the decode of iteration m starts after its own DFT)
     const bool sig_major = !p->sm_fold.empty();
+    // BF16X3 after the signal-major fold: the DFTs of all iterations in grouped launches
+    // (the tensor-core DFT holds whole SMs; two launches instead of one or two per iteration)
+    const bool all_dft = sig_major && p->uall;
     if (sig_major) {
         rc = launch_fold_signal_major(p, nsig, x, x_stride, st);
         if (rc) return rc;
     }
+    if (all_dft) {
+        std::vector<DftStrided> sets(ni);
+        for (size_t mi = 0; mi < ni; ++mi) {
+            const IterHost& ih = p->iters[mi];
+            const Window& w = p->wins[ih.win];
+            sets[mi] = DftStrided{ih.d.B, ih.d.R, nsig, p->zall + p->yoff[mi], p->ytot, p->uall + p->yoff[mi],
+                                  p->ytot, p->y + p->yoff[mi], p->ytot, w.dA1, w.dA2, w.tw4};
+        }
+        cudaEvent_t ev = nullptr;
+        rc = prof_begin(p, st, &ev);
+        if (!rc) rc = launch_dft_tc_strided(sets.data(), (int)ni, p->status, p->sm_count, st);
+        if (!rc) rc = prof_end(p, st, ev, kProfFft, 0);
+        if (!rc) rc = check_cuda(cudaEventRecord(p->ev[1], st));
+        if (!rc) rc = check_cuda(cudaStreamWaitEvent(ds, p->ev[1], 0));
+        if (rc) return rc;
+    }
     for (size_t mi = 0; mi < ni; ++mi) {
         float2* ym = p->y + p->yoff[mi];
-        rc = sig_major ? launch_iter_dft(p, (int)mi, nsig, p->zall + p->yoff[mi], p->ytot, ym, p->ytot, st)
-                       : launch_bucketize(p, (int)mi, nsig, x, x_stride, 0, ym, p->ytot, st);
-        if (!rc) rc = check_cuda(cudaEventRecord(p->ev[1 + mi], st));
-        if (!rc) rc = check_cuda(cudaStreamWaitEvent(ds, p->ev[1 + mi], 0));
-        if (rc) return rc;
+        if (!all_dft) {
+            rc = sig_major ? launch_iter_dft(p, (int)mi, nsig, p->zall + p->yoff[mi], p->ytot, ym, p->ytot, st)
+                           : launch_bucketize(p, (int)mi, nsig, x, x_stride, 0, ym, p->ytot, st);
+            if (!rc) rc = check_cuda(cudaEventRecord(p->ev[1 + mi], st));
+            if (!rc) rc = check_cuda(cudaStreamWaitEvent(ds, p->ev[1 + mi], 0));
+            if (rc) return rc;
+        }
         const IterDev& d = p->iters[mi].d;
         if (p->o.trace) {
             rc = check_cuda(cudaMemcpyAsync(p->trace_y + mi * rb, ym, (size_t)d.R * d.B * sizeof(float2),

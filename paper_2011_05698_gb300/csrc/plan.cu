@@ -124,7 +124,7 @@ void free_plan(sfft4_plan_s* p) {
             cudaFree(w.tw4);
         }
     }
-    void* bufs[] = {p->iters_dev, p->z, p->zall, p->y, p->u, p->status, p->F, p->ff, p->fv, p->fvotes, p->hkeys,
+    void* bufs[] = {p->iters_dev, p->z, p->zall, p->uall, p->y, p->u, p->status, p->F, p->ff, p->fv, p->fvotes, p->hkeys,
                     p->hvals, p->theta, p->fxexp, p->trace_y, p->trace_F, p->trace_ff,
                     p->trace_fv, p->trace_votes};
     for (void* b : bufs) cudaFree(b);
@@ -185,9 +185,15 @@ int32_t uniform_kernels(const sfft4_plan_s* p) {
     const bool sig_major = p->o.fold_order == SFFT4_FOLD_SIGNAL_MAJOR;
     // finalize, and the fold launches covering every iteration (signal-major)
     int32_t k = 1 + (sig_major ? std::max<int32_t>(1, (int32_t)p->sm_fold.size()) : 0);
-    for (auto& ih : p->iters)
-        k += (sig_major ? 0 : (int32_t)ih.groups.size()) + 1 +
-             ((p->o.precision == SFFT4_BF16X3 && ih.d.B > 64) ? 2 : 1);
+    const bool tc = p->o.precision == SFFT4_BF16X3;
+    int nsingle = 0, nfour = 0;  // BF16X3 DFT groups by stage count
+    for (auto& ih : p->iters) {
+        k += (sig_major ? 0 : (int32_t)ih.groups.size()) + 1;  // folds, decode
+        if (!(sig_major && tc)) k += (tc && ih.d.B > 64) ? 2 : 1;
+        (ih.d.B > 64 ? nfour : nsingle)++;
+    }
+    // signal-major BF16X3: every iteration's DFT in grouped launches of up to 12 groups
+    if (sig_major && tc) k += (nsingle + nfour + 11) / 12 + (nfour + 11) / 12;
     return k;
 }
 
@@ -447,6 +453,7 @@ int sfft4_plan(sfft4_plan_t* out, int64_t N, int64_t K, int32_t l, double q, uin
     CK(cudaMalloc(&p->y, mb * (size_t)p->ytot * sizeof(float2)));
     if (o.fold_order == SFFT4_FOLD_SIGNAL_MAJOR) {
         CK(cudaMalloc(&p->zall, mb * (size_t)p->ytot * sizeof(float2)));
+        if (o.precision == SFFT4_BF16X3) CK(cudaMalloc(&p->uall, mb * (size_t)p->ytot * sizeof(float2)));
         const int rcs = sfft4::build_signal_major_fold(p);
         if (rcs) { free_plan(p); return rcs; }
     }

@@ -229,6 +229,7 @@ struct sfft4_plan_s {
     // group) with z of iteration m at zall + yoff[m] (per-signal stride ytot); a launch's grid
     // is nsig x ntiles CTAs, the ntiles (job, residue slice) tiles of a signal adjacent
     float2* zall = nullptr;     // [sig][ytot] folded arrays of every iteration
+    float2* uall = nullptr;     // [sig][ytot] four-step scratch of every iteration (BF16X3)
     std::vector<sfft4::SigFoldHost> sm_fold;  // launches (more than one past kSigJobs jobs)
     // asynchronous executes (sfft4_execute_batched_async): two workspaces, this plan's and a
     // peer plan's, used in turn on their own streams; ev_done[s] marks slot s's latest execute
@@ -321,6 +322,21 @@ int plan_tables(sfft4_plan_s* p, std::vector<Window>* cache);
 size_t dft_tc_matrix_bytes();
 int build_dft_tc_tables(int B, unsigned char* A1, unsigned char* A2, float2* tw4);
 int configure_dft_tc();
+// One iteration's DFT columns for launch_dft_tc_strided: signal s's R x B arrays at
+// z + s z_stride (input), u + s u_stride (four-step scratch), y + s y_stride (output).
+struct DftStrided {
+    int32_t B, R, nsig;
+    const float2* z;
+    int64_t z_stride;
+    float2* u;
+    int64_t u_stride;
+    float2* y;
+    int64_t y_stride;
+    const unsigned char* A1;
+    const unsigned char* A2;
+    const float2* tw4;
+};
+int launch_dft_tc_strided(const DftStrided* sets, int nsets, int32_t* status, int sm_count, cudaStream_t st);
 int launch_dft_tc(const float2* z, int64_t z_stride, float2* u, int64_t u_stride, float2* y, int64_t y_stride, int nsig,
                   int R, int B, const unsigned char* A1, const unsigned char* A2, const float2* tw4,
                   int32_t* status, int sm_count, cudaStream_t st);
