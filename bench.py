@@ -195,7 +195,8 @@ def device_batch(N, K, S, seed0, snr, device):
 def uneven_form(s4, args, dev, stream, dist):
     """The uneven batch: 512 signals, N log-uniform over 2^16..2^22, K log-uniform in
     [10, 2000] capped at N/64, SNR uniform in [10, 40] dB; one BatchPlan execute per step,
-    replayed as a CUDA graph, BF16x3 DFT.  Kernel times come from a second, profiled plan."""
+    replayed as a CUDA graph, BF16x3 DFT, asynchronous (consecutive steps overlap; the
+    synchronous form is reported beside it).  Kernel times come from a second, profiled plan."""
     import torch
     from synth.signals import device_signal, signal_seed, uneven_sizes
     nsig, seed = args.uneven_signals, 2026
@@ -218,15 +219,30 @@ def uneven_form(s4, args, dev, stream, dist):
     bp = s4.BatchPlan(Ns.tolist(), Ks.tolist(), L_DEF, Q_DEF, seed=seed, precision=args.precision, graph=graph,
                       B1s=B1s)
     out = bp.outputs()
+    outs = [out, bp.outputs()]
     ptrs = bp.pointers(xs)
+    pipelined = not args.no_async
+    counter = [0]
 
     def step():
-        bp.execute(xs, out=out, ptrs=ptrs)
+        # pipelined: asynchronous executes, two workspaces in turn (one batch's decode chain
+        # overlaps the next batch's gathers)
+        if pipelined:
+            bp.execute(xs, out=outs[counter[0] % 2], ptrs=ptrs, asynchronous=True)
+            counter[0] += 1
+        else:
+            bp.execute(xs, out=out, ptrs=ptrs)
 
     steps = max(3, min(args.steps, 20))
-    el = max_over_ranks(timed(step, steps, args.warmup, stream, dist), dist, dev)
+    el = max_over_ranks(timed(step, steps, args.warmup, stream, dist, finish=bp.wait if pipelined else None),
+                        dist, dev)
     world = dist.get_world_size() if dist is not None else 1
     info = dict(bp.info)
+    sync = None
+    if pipelined:
+        es = max_over_ranks(timed(lambda: bp.execute(xs, out=out, ptrs=ptrs), steps, 2, stream, dist), dist, dev)
+        sync = {"value": nsig * steps * world / es, "ms_per_step": 1e3 * es / steps,
+                "form": "one synchronous execute per step (graph replay)" if graph else "one synchronous execute per step"}
     bp.close()
     # the same launches issued directly (no graph), for comparison
     direct = None
@@ -254,6 +270,7 @@ def uneven_form(s4, args, dev, stream, dist):
             "graph_launches_per_step": 1 if graph else 0, "levels": info["n_levels"], "classes": info["n_classes"],
             "workload": "512 signals: N=2^n, n uniform on 16..22; K=round(exp U[ln 10, ln 2000]) <= N/64; "
                         "SNR U[10, 40] dB; l=16, q=1",
+            "pipelined": pipelined, "synchronous": sync,
             "fold_gbs_useful": fold_gbs, "autotune": tune, "direct_launches": direct,
             "kernel_ms_one_execute": {k: prof[k + "_ms"] for k in ("fold", "fft", "decode", "finalize")}}
 

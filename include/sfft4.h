@@ -15,7 +15,9 @@
  * work queued on the given stream has completed.  Execution is asynchronous on the
  * caller's stream (a cudaStream_t passed as void*; NULL = the legacy default stream).
  * A plan is not thread-safe: do not execute one plan concurrently from two host threads
- * or on two streams at once (its workspace is shared by all its executions).
+ * or on two streams at once (its workspace is shared by all its executions).  The
+ * asynchronous executes (sfft4_execute_batched_async, sfft4_execute_batched_v_async) are the
+ * exception: they alternate two workspaces on the plan's own streams by themselves.
  */
 #ifndef SFFT4_H
 #define SFFT4_H
@@ -174,7 +176,7 @@ SFFT4_API int sfft4_execute_batched_async(sfft4_plan_t plan, int32_t nsig, const
                                           int64_t* idx_dev, sfft4_c128* val_dev, int64_t* nfound_dev,
                                           int8_t* votes_dev, void* stream);
 
-/* Makes `stream` wait for every sfft4_execute_batched_async call issued so far on the plan.
+/* Makes `stream` wait for every asynchronous execute issued so far on the plan.
  * Errors: SFFT4_EINVAL, SFFT4_ECUDA. */
 SFFT4_API int sfft4_wait(sfft4_plan_t plan, void* stream);
 
@@ -210,6 +212,19 @@ SFFT4_API int sfft4_plan_batched(sfft4_plan_t* out, int32_t nsig, const int64_t*
 SFFT4_API int sfft4_execute_batched_v(sfft4_plan_t plan, const void* const* x_ptrs_dev, int64_t* idx_dev,
                                       sfft4_c128* val_dev, int64_t* nfound_dev, int8_t* votes_dev,
                                       void* stream);
+
+/*
+ * sfft4_execute_batched_v_async -- sfft4_execute_batched_v as a pipeline of batches, with the
+ * rules of sfft4_execute_batched_async: the call runs on the plan's own streams after the
+ * work queued on `stream`, two workspaces in turn (the first call makes the second, a plan of
+ * the same signals and options), results complete after sfft4_wait.  The pointer table, the
+ * signals and the outputs of a call must stay valid and unmodified until then.
+ * Errors: SFFT4_EINVAL, SFFT4_ESTATE (not a plan of sfft4_plan_batched), SFFT4_ENOMEM,
+ * SFFT4_ECUDA.
+ */
+SFFT4_API int sfft4_execute_batched_v_async(sfft4_plan_t plan, const void* const* x_ptrs_dev, int64_t* idx_dev,
+                                            sfft4_c128* val_dev, int64_t* nfound_dev, int8_t* votes_dev,
+                                            void* stream);
 
 typedef struct {
     int32_t nsig;

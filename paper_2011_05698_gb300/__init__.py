@@ -336,14 +336,22 @@ class BatchPlan:
         self._ptrs.copy_(host, non_blocking=False)
         return self._ptrs
 
-    def execute(self, xs, out=None, ptrs=None):
+    def execute(self, xs, out=None, ptrs=None, asynchronous=False):
         """Transforms of the signals xs (list of CUDA complex64 tensors, xs[i] of length N_i).
-        Returns (idx, val, nfound, votes), rows of length Kmax; row i past K_i holds -1 / 0."""
+        Returns (idx, val, nfound, votes), rows of length Kmax; row i past K_i holds -1 / 0.
+        asynchronous=True: the batch runs on the plan's own streams and overlaps the next
+        call (two workspaces in turn); results are complete after wait(), and xs, ptrs and
+        the outputs must stay untouched until then."""
         if ptrs is None:
             ptrs = self.pointers(xs)
         idx, val, nf, votes = out if out is not None else self.outputs()
-        check(_lib.load().sfft4_execute_batched_v(self._h, ctypes.c_void_p(ptrs.data_ptr()),
-                                                  ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(val.data_ptr()),
-                                                  ctypes.c_void_p(nf.data_ptr()), ctypes.c_void_p(votes.data_ptr()),
-                                                  _stream_ptr(self.device)), "sfft4_execute_batched_v")
+        fn = "sfft4_execute_batched_v_async" if asynchronous else "sfft4_execute_batched_v"
+        check(getattr(_lib.load(), fn)(self._h, ctypes.c_void_p(ptrs.data_ptr()),
+                                       ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(val.data_ptr()),
+                                       ctypes.c_void_p(nf.data_ptr()), ctypes.c_void_p(votes.data_ptr()),
+                                       _stream_ptr(self.device)), fn)
         return idx, val, nf, votes
+
+    def wait(self):
+        """Makes the current stream wait for every asynchronous execute issued so far."""
+        check(_lib.load().sfft4_wait(self._h, _stream_ptr(self.device)), "sfft4_wait")

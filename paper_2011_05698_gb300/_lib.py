@@ -87,6 +87,7 @@ SIGNATURES = [
                                           ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
                                           ctypes.c_int32, ctypes.c_double, ctypes.c_uint64, ctypes.POINTER(Opts)]),
     ("sfft4_execute_batched_v", ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    ("sfft4_execute_batched_v_async", ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     ("sfft4_get_batch_info", ctypes.c_int, [_P, ctypes.POINTER(BatchInfo)]),
     ("sfft4_get_plan_info", ctypes.c_int, [_P, ctypes.POINTER(PlanInfo)]),
     ("sfft4_get_iter_info", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(IterInfo)]),

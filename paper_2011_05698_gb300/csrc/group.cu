@@ -384,6 +384,8 @@ int sfft4_execute_batched_v(sfft4_plan_t p, const void* const* x_ptrs_dev, int64
                             sfft4_c128* val_dev, int64_t* nfound_dev, int8_t* votes_dev, void* stream) {
     if (!p || !x_ptrs_dev || !idx_dev || !val_dev || !nfound_dev) return SFFT4_EINVAL;
     if (!p->grp) return SFFT4_ESTATE;
+    int rc0 = join_slot0(p, (cudaStream_t)stream);
+    if (rc0) return rc0;
     const GroupRun r{(const float2* const*)x_ptrs_dev, idx_dev, val_dev, nfound_dev, votes_dev};
     const uint64_t key[8] = {2, (uint64_t)(uintptr_t)x_ptrs_dev, (uint64_t)(uintptr_t)idx_dev,
                              (uint64_t)(uintptr_t)val_dev, (uint64_t)(uintptr_t)nfound_dev,
@@ -395,6 +397,18 @@ int sfft4_execute_batched_v(sfft4_plan_t p, const void* const* x_ptrs_dev, int64
         p->n_transforms += p->grp->nsig;
         p->last_nsig = p->grp->nsig;
     }
+    return rc;
+}
+
+int sfft4_execute_batched_v_async(sfft4_plan_t p, const void* const* x_ptrs_dev, int64_t* idx_dev,
+                                  sfft4_c128* val_dev, int64_t* nfound_dev, int8_t* votes_dev, void* stream) {
+    if (!p || !x_ptrs_dev || !idx_dev || !val_dev || !nfound_dev) return SFFT4_EINVAL;
+    if (!p->grp) return SFFT4_ESTATE;
+    sfft4_plan_s* w = nullptr;
+    cudaStream_t as = nullptr;
+    int rc = async_begin(p, (cudaStream_t)stream, &w, &as);
+    if (!rc) rc = sfft4_execute_batched_v(w, x_ptrs_dev, idx_dev, val_dev, nfound_dev, votes_dev, as);
+    if (!rc) rc = async_end(p, as);
     return rc;
 }
 

@@ -1602,6 +1602,44 @@ int configure_kernels() {
     return rc;
 }
 
+int join_slot0(sfft4_plan_s* p, cudaStream_t st) {
+    return (p->async_used & 1) ? check_cuda(cudaStreamWaitEvent(st, p->ev_done[0], 0)) : SFFT4_OK;
+}
+
+// Two workspaces used in turn: this plan's (slot 0) and a peer plan of the same transform
+// (slot 1), each on its own stream; slot s's previous execute is ahead on that stream.
+int async_begin(sfft4_plan_s* p, cudaStream_t caller, sfft4_plan_s** w, cudaStream_t* as) {
+    int rc = SFFT4_OK;
+    if (!p->peer) {
+        if (p->grp)
+            rc = sfft4_plan_batched(&p->peer, (int32_t)p->bN.size(), p->bN.data(), p->bK.data(),
+                                    p->bB1.empty() ? nullptr : p->bB1.data(), p->l, p->bq, p->seed, &p->bopts);
+        else
+            rc = sfft4_plan(&p->peer, p->N, p->K, p->l, (double)p->qn / kQDen, p->seed, &p->o);
+        for (int s = 0; s < 2 && !rc; ++s) {
+            rc = check_cuda(cudaStreamCreateWithFlags(&p->astream[s], cudaStreamNonBlocking));
+            if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&p->ev_in[s], cudaEventDisableTiming));
+            if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&p->ev_done[s], cudaEventDisableTiming));
+        }
+        if (rc) return rc;
+    }
+    const int s = p->async_next;
+    *w = s ? p->peer : p;
+    *as = p->astream[s];
+    rc = check_cuda(cudaEventRecord(p->ev_in[s], caller));
+    if (!rc) rc = check_cuda(cudaStreamWaitEvent(*as, p->ev_in[s], 0));
+    return rc;
+}
+
+int async_end(sfft4_plan_s* p, cudaStream_t as) {
+    const int s = p->async_next;
+    const int rc = check_cuda(cudaEventRecord(p->ev_done[s], as));
+    if (rc) return rc;
+    p->async_used |= 1 << s;
+    p->async_next = s ^ 1;
+    return SFFT4_OK;
+}
+
 int graph_run(sfft4_plan_s* p, const uint64_t key[8], cudaStream_t st,
               int (*body)(sfft4_plan_s*, const void*, cudaStream_t), const void* ctx) {
     int rc = configure_kernels();
@@ -1743,11 +1781,6 @@ int run(sfft4_plan_s* p, int nsig, const float2* x, int64_t x_stride, int64_t* i
 
 extern "C" {
 
-// A synchronous execute uses the plan's own workspace (slot 0 of the asynchronous ones).
-static int join_slot0(sfft4_plan_s* p, cudaStream_t st) {
-    return (p->async_used & 1) ? check_cuda(cudaStreamWaitEvent(st, p->ev_done[0], 0)) : SFFT4_OK;
-}
-
 int sfft4_execute(sfft4_plan_t p, const void* x_dev, int64_t* idx_dev, sfft4_c128* val_dev,
                   int64_t* nfound_dev, int8_t* votes_dev, void* stream) {
     if (!p || !x_dev || !idx_dev || !val_dev || !nfound_dev) return SFFT4_EINVAL;
@@ -1763,31 +1796,12 @@ int sfft4_execute_batched_async(sfft4_plan_t p, int32_t nsig, const void* x_dev,
     if (!p || !x_dev || !idx_dev || !val_dev || !nfound_dev) return SFFT4_EINVAL;
     if (p->grp || p->o.trace) return SFFT4_ESTATE;
     if (nsig < 1 || nsig > p->o.max_batch || x_stride < p->N) return SFFT4_EINVAL;
-    int rc = SFFT4_OK;
-    if (!p->peer) {
-        // the second workspace: a plan of the same transform and options
-        rc = sfft4_plan(&p->peer, p->N, p->K, p->l, (double)p->qn / kQDen, p->seed, &p->o);
-        if (rc) return rc;
-        for (int s = 0; s < 2 && !rc; ++s) {
-            rc = check_cuda(cudaStreamCreateWithFlags(&p->astream[s], cudaStreamNonBlocking));
-            if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&p->ev_in[s], cudaEventDisableTiming));
-            if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&p->ev_done[s], cudaEventDisableTiming));
-        }
-        if (rc) return rc;
-    }
-    const int s = p->async_next;
-    sfft4_plan_s* w = s ? p->peer : p;
-    cudaStream_t as = p->astream[s];
-    // the execute reads x after the work queued on `stream` so far; slot s's previous execute
-    // is ahead of it on the slot's stream
-    rc = check_cuda(cudaEventRecord(p->ev_in[s], (cudaStream_t)stream));
-    if (!rc) rc = check_cuda(cudaStreamWaitEvent(as, p->ev_in[s], 0));
+    sfft4_plan_s* w = nullptr;
+    cudaStream_t as = nullptr;
+    int rc = async_begin(p, (cudaStream_t)stream, &w, &as);
     if (!rc) rc = run(w, nsig, (const float2*)x_dev, x_stride, idx_dev, val_dev, nfound_dev, votes_dev, as);
-    if (!rc) rc = check_cuda(cudaEventRecord(p->ev_done[s], as));
-    if (rc) return rc;
-    p->async_used |= 1 << s;
-    p->async_next = s ^ 1;
-    return SFFT4_OK;
+    if (!rc) rc = async_end(p, as);
+    return rc;
 }
 
 int sfft4_wait(sfft4_plan_t p, void* stream) {

@@ -513,6 +513,12 @@ int sfft4_plan_batched(sfft4_plan_t* out, int32_t nsig, const int64_t* N, const 
     CK(cudaMemset(p->status, 0, sizeof(int32_t)));
     int rc = build_group_plan(p, nsig, N, K, B1, l, q, seed, opts);
     if (rc) { free_plan(p); return rc; }
+    p->bN.assign(N, N + nsig);
+    p->bK.assign(K, K + nsig);
+    if (B1) p->bB1.assign(B1, B1 + nsig);
+    p->bq = q;
+    if (opts) p->bopts = *opts;
+    else sfft4_opts_default(&p->bopts);
     CK(cudaStreamCreateWithFlags(&p->dstream, cudaStreamNonBlocking));
     p->ev.assign(group_levels(p->grp) + 2, nullptr);
     for (auto& e : p->ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));

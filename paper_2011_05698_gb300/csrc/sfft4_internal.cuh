@@ -234,6 +234,10 @@ struct sfft4_plan_s {
     // asynchronous executes (sfft4_execute_batched_async): two workspaces, this plan's and a
     // peer plan's, used in turn on their own streams; ev_done[s] marks slot s's latest execute
     sfft4_plan_s* peer = nullptr;
+    std::vector<int64_t> bN, bK;        // sfft4_plan_batched's arguments (to make the peer)
+    std::vector<int32_t> bB1;
+    double bq = 0;
+    sfft4_opts bopts;
     cudaStream_t astream[2] = {nullptr, nullptr};
     cudaEvent_t ev_in[2] = {nullptr, nullptr};
     cudaEvent_t ev_done[2] = {nullptr, nullptr};
@@ -288,6 +292,12 @@ DecodeArgs make_decode_args(const sfft4_plan_s* p, int mi);
 size_t decode_smem_bytes(int B);
 int configure_kernels();
 int build_signal_major_fold(sfft4_plan_s* p);
+// Workspace and stream of the next asynchronous execute (makes the peer plan on first use),
+// after the execute reads its inputs behind the work queued on `caller`; async_end marks it.
+int async_begin(sfft4_plan_s* p, cudaStream_t caller, sfft4_plan_s** w, cudaStream_t* as);
+int async_end(sfft4_plan_s* p, cudaStream_t as);
+// A synchronous execute waits for the asynchronous one that used the plan's own workspace.
+int join_slot0(sfft4_plan_s* p, cudaStream_t st);
 int launch_fold_signal_major(sfft4_plan_s* p, int nsig, const float2* x, int64_t x_stride, cudaStream_t st);
 int launch_fold_multi(int RG, const FoldArgs* jobs, const FoldTile* tiles, int ntiles,
                       const float2* const* xptrs, int threads, size_t smem, cudaStream_t st);

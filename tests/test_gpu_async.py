@@ -105,3 +105,29 @@ def test_async_rejects_trace_plans(s4):
     with pytest.raises(Sfft4Error):
         p.execute_batched(batch(range(2), None), asynchronous=True)
     p.close()
+
+
+def test_uneven_batch_async_equals_synchronous(s4):
+    """Batches of signals of different N and K (sfft4_execute_batched_v_async): three batches
+    of different contents in flight through two workspaces, each bit-identical to a
+    synchronous execute, with and without graph replay."""
+    import torch
+    from synth.signals import device_signal
+    sizes = [(2**14, 16), (2**16, 50), (2**12, 8), (2**18, 200), (2**14, 256), (2**20, 100)]
+    Ns, Ks = [n for n, _ in sizes], [k for _, k in sizes]
+    for graph in (False, True):
+        bp = s4.BatchPlan(Ns, Ks, L_, Q_, seed=9, precision="bf16x3", graph=graph)
+        sets = [[device_signal(n, k, 1000 * b + i, 20.0, "cuda")[0] for i, (n, k) in enumerate(sizes)]
+                for b in range(3)]
+        ptrs = [bp.pointers(xs) for xs in sets]
+        want = [host(bp.execute(xs, ptrs=pt)) for xs, pt in zip(sets, ptrs)]
+        outs = [bp.outputs() for _ in sets]
+        for xs, pt, o in zip(sets, ptrs, outs):
+            bp.execute(xs, out=o, ptrs=pt, asynchronous=True)
+        bp.wait()
+        torch.cuda.synchronize()
+        for w, o in zip(want, outs):
+            assert same(w, host(o))
+        st = bp.stats()
+        assert st["executes"] == 6 and st["transforms"] == 6 * len(sizes)
+        bp.close()

@@ -123,6 +123,7 @@ def test_execute_rejects_null_arguments(lib):
     assert lib.sfft4_stats(None, None) == _lib.SFFT4_EINVAL
     assert lib.sfft4_execute_batched_async(None, 1, None, 0, None, None, None, None, None) == _lib.SFFT4_EINVAL
     assert lib.sfft4_wait(None, None) == _lib.SFFT4_EINVAL
+    assert lib.sfft4_execute_batched_v_async(None, None, None, None, None, None, None) == _lib.SFFT4_EINVAL
     lib.sfft4_destroy(None)
 
 
