@@ -74,7 +74,9 @@ typedef struct {
     double mag_tol;          /* magnitude consistency of a vote; default 0.5              */
     int32_t max_iters;       /* cap on the static schedule length; default 64             */
     int32_t max_batch;       /* most signals one sfft4_execute_batched call may pass;
-                                sizes the workspace; default 1                            */
+                                sizes the workspace; with the signal-major fold, max_batch
+                                x the fold tiles of one signal must stay below 2^31 (one
+                                launch grid), else SFFT4_EINVAL; default 1                  */
     int32_t trace;           /* nonzero: keep per-iteration bucket arrays and found sets
                                 of signal 0 for sfft4_trace_get (tests); default 0         */
     int32_t profile;         /* nonzero: bracket each kernel launch of an execute with CUDA

@@ -1610,18 +1610,23 @@ int join_slot0(sfft4_plan_s* p, cudaStream_t st) {
 // (slot 1), each on its own stream; slot s's previous execute is ahead on that stream.
 int async_begin(sfft4_plan_s* p, cudaStream_t caller, sfft4_plan_s** w, cudaStream_t* as) {
     int rc = SFFT4_OK;
+    // streams and events first (kept if the peer fails, and made again only where missing),
+    // then the peer; p->peer is set only when every piece exists
+    for (int s = 0; s < 2 && !rc; ++s) {
+        if (!p->astream[s]) rc = check_cuda(cudaStreamCreateWithFlags(&p->astream[s], cudaStreamNonBlocking));
+        if (!rc && !p->ev_in[s]) rc = check_cuda(cudaEventCreateWithFlags(&p->ev_in[s], cudaEventDisableTiming));
+        if (!rc && !p->ev_done[s]) rc = check_cuda(cudaEventCreateWithFlags(&p->ev_done[s], cudaEventDisableTiming));
+    }
+    if (rc) return rc;
     if (!p->peer) {
+        sfft4_plan_s* peer = nullptr;
         if (p->grp)
-            rc = sfft4_plan_batched(&p->peer, (int32_t)p->bN.size(), p->bN.data(), p->bK.data(),
+            rc = sfft4_plan_batched(&peer, (int32_t)p->bN.size(), p->bN.data(), p->bK.data(),
                                     p->bB1.empty() ? nullptr : p->bB1.data(), p->l, p->bq, p->seed, &p->bopts);
         else
-            rc = sfft4_plan(&p->peer, p->N, p->K, p->l, (double)p->qn / kQDen, p->seed, &p->o);
-        for (int s = 0; s < 2 && !rc; ++s) {
-            rc = check_cuda(cudaStreamCreateWithFlags(&p->astream[s], cudaStreamNonBlocking));
-            if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&p->ev_in[s], cudaEventDisableTiming));
-            if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&p->ev_done[s], cudaEventDisableTiming));
-        }
+            rc = sfft4_plan(&peer, p->N, p->K, p->l, (double)p->qn / kQDen, p->seed, &p->o);
         if (rc) return rc;
+        p->peer = peer;
     }
     const int s = p->async_next;
     *w = s ? p->peer : p;
