@@ -219,16 +219,16 @@ def uneven_form(s4, args, dev, stream, dist):
     bp = s4.BatchPlan(Ns.tolist(), Ks.tolist(), L_DEF, Q_DEF, seed=seed, precision=args.precision, graph=graph,
                       B1s=B1s)
     out = bp.outputs()
-    outs = [out, bp.outputs()]
+    outs = [out, bp.outputs(), bp.outputs()]  # one per batch in flight
     ptrs = bp.pointers(xs)
     pipelined = not args.no_async
     counter = [0]
 
     def step():
-        # pipelined: asynchronous executes, two workspaces in turn (one batch's decode chain
-        # overlaps the next batch's gathers)
+        # pipelined: asynchronous executes, three workspaces in turn (the decode chains of
+        # two batches overlap each other and the next batch's gathers)
         if pipelined:
-            bp.execute(xs, out=outs[counter[0] % 2], ptrs=ptrs, asynchronous=True)
+            bp.execute(xs, out=outs[counter[0] % len(outs)], ptrs=ptrs, asynchronous=True)
             counter[0] += 1
         else:
             bp.execute(xs, out=out, ptrs=ptrs)
@@ -576,7 +576,7 @@ def main():
                    precision=args.precision, fold_order=args.fold_order)
     xs = device_batch(N_DEF, K_DEF, S, rank_seed0(rank), args.snr, dev)
     out = plan._outputs(S)
-    outs = [out, plan._outputs(S)]
+    outs = [out, plan._outputs(S)]  # one per batch in flight
     stream = torch.cuda.current_stream(dev)
     pipelined = not args.no_async
     counter = [0]
@@ -585,7 +585,7 @@ def main():
         # one batch per step; pipelined: asynchronous executes (two workspaces in turn), so
         # the decode chain of one batch overlaps the gather of the next
         if pipelined:
-            plan.execute_batched(xs, outs[counter[0] % 2], asynchronous=True)
+            plan.execute_batched(xs, outs[counter[0] % len(outs)], asynchronous=True)
             counter[0] += 1
         else:
             plan.execute_batched(xs, out)

@@ -17,7 +17,8 @@
  * A plan is not thread-safe: do not execute one plan concurrently from two host threads
  * or on two streams at once (its workspace is shared by all its executions).  The
  * asynchronous executes (sfft4_execute_batched_async, sfft4_execute_batched_v_async) are the
- * exception: they alternate two workspaces on the plan's own streams by themselves.
+ * exception: they alternate two (uniform batches) or three (batches of uneven signals)
+ * workspaces on the plan's own streams by themselves.
  */
 #ifndef SFFT4_H
 #define SFFT4_H
@@ -165,7 +166,8 @@ SFFT4_API int sfft4_execute_batched(sfft4_plan_t plan, int32_t nsig, const void*
  * the work queued on `stream` so far, and `stream` does not wait for them, so consecutive
  * calls overlap (the decode chain of one batch with the gather of the next).  Calls use two
  * workspaces in turn; the first call allocates the second (a plan of the same transform and
- * options, created synchronously).  A third call queues behind the first one's work.
+ * options, created synchronously).  A third call queues behind the first one's work, so at
+ * most two calls are in flight.
  *   Results are complete once sfft4_wait(plan, s) has been issued on a stream s and s has
  *   reached that point.  x_dev and the output buffers of a call must stay valid and
  *   unmodified until then; calls in flight together need distinct output buffers.
@@ -217,9 +219,9 @@ SFFT4_API int sfft4_execute_batched_v(sfft4_plan_t plan, const void* const* x_pt
 
 /*
  * sfft4_execute_batched_v_async -- sfft4_execute_batched_v as a pipeline of batches, with the
- * rules of sfft4_execute_batched_async: the call runs on the plan's own streams after the
- * work queued on `stream`, two workspaces in turn (the first call makes the second, a plan of
- * the same signals and options), results complete after sfft4_wait.  The pointer table, the
+ * rules of sfft4_execute_batched_async, but with three workspaces in turn (the first call
+ * makes the other two, plans of the same signals and options), so that the decode chains of
+ * two batches overlap; at most three calls are in flight; results complete after sfft4_wait.  The pointer table, the
  * signals and the outputs of a call must stay valid and unmodified until then.
  * Errors: SFFT4_EINVAL, SFFT4_ESTATE (not a plan of sfft4_plan_batched), SFFT4_ENOMEM,
  * SFFT4_ECUDA.

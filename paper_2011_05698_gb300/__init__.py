@@ -194,9 +194,9 @@ class Plan:
     def execute_batched(self, xs, out=None, asynchronous=False):
         """Transforms of each row of xs (shape (nsig, N), complex64, on the device).  With
         asynchronous=True the batch runs on the plan's own streams and overlaps the next call
-        (two workspaces in turn); its results are complete after wait().  xs and the outputs
-        must then stay untouched until wait(), and calls in flight together need distinct
-        output buffers."""
+        (two workspaces in turn, up to two batches in flight); its results are complete after
+        wait().  xs and the outputs must then stay untouched until wait(), and calls in flight
+        together need distinct output buffers."""
         self._check_x(xs, 2)
         nsig = xs.shape[0]
         idx, val, nf, votes = out if out is not None else self._outputs(nsig)
@@ -340,8 +340,8 @@ class BatchPlan:
         """Transforms of the signals xs (list of CUDA complex64 tensors, xs[i] of length N_i).
         Returns (idx, val, nfound, votes), rows of length Kmax; row i past K_i holds -1 / 0.
         asynchronous=True: the batch runs on the plan's own streams and overlaps the next
-        call (two workspaces in turn); results are complete after wait(), and xs, ptrs and
-        the outputs must stay untouched until then."""
+        call (three workspaces in turn, up to three batches in flight); results are complete
+        after wait(), and xs, ptrs and the outputs must stay untouched until then."""
         if ptrs is None:
             ptrs = self.pointers(xs)
         idx, val, nf, votes = out if out is not None else self.outputs()

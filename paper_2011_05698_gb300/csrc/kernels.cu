@@ -1606,19 +1606,22 @@ int join_slot0(sfft4_plan_s* p, cudaStream_t st) {
     return (p->async_used & 1) ? check_cuda(cudaStreamWaitEvent(st, p->ev_done[0], 0)) : SFFT4_OK;
 }
 
-// Two workspaces used in turn: this plan's (slot 0) and a peer plan of the same transform
-// (slot 1), each on its own stream; slot s's previous execute is ahead on that stream.
+// async_depth workspaces used in turn: this plan's (slot 0) and peer plans of the same
+// transform (slots 1..), each on its own stream; slot s's previous execute is ahead on that
+// stream, so that many batches can be in flight.
 int async_begin(sfft4_plan_s* p, cudaStream_t caller, sfft4_plan_s** w, cudaStream_t* as) {
     int rc = SFFT4_OK;
-    // streams and events first (kept if the peer fails, and made again only where missing),
-    // then the peer; p->peer is set only when every piece exists
-    for (int s = 0; s < 2 && !rc; ++s) {
+    // streams and events first (kept if a peer fails, and made again only where missing),
+    // then the peers; a peer is stored only once it exists
+    for (int s = 0; s < kAsyncDepth && !rc; ++s) {
         if (!p->astream[s]) rc = check_cuda(cudaStreamCreateWithFlags(&p->astream[s], cudaStreamNonBlocking));
         if (!rc && !p->ev_in[s]) rc = check_cuda(cudaEventCreateWithFlags(&p->ev_in[s], cudaEventDisableTiming));
         if (!rc && !p->ev_done[s]) rc = check_cuda(cudaEventCreateWithFlags(&p->ev_done[s], cudaEventDisableTiming));
     }
     if (rc) return rc;
-    if (!p->peer) {
+    const int depth = async_depth(p->grp != nullptr);
+    for (int i = 0; i < depth - 1; ++i) {
+        if (p->peer[i]) continue;
         sfft4_plan_s* peer = nullptr;
         if (p->grp)
             rc = sfft4_plan_batched(&peer, (int32_t)p->bN.size(), p->bN.data(), p->bK.data(),
@@ -1626,10 +1629,10 @@ int async_begin(sfft4_plan_s* p, cudaStream_t caller, sfft4_plan_s** w, cudaStre
         else
             rc = sfft4_plan(&peer, p->N, p->K, p->l, (double)p->qn / kQDen, p->seed, &p->o);
         if (rc) return rc;
-        p->peer = peer;
+        p->peer[i] = peer;
     }
     const int s = p->async_next;
-    *w = s ? p->peer : p;
+    *w = s ? p->peer[s - 1] : p;
     *as = p->astream[s];
     rc = check_cuda(cudaEventRecord(p->ev_in[s], caller));
     if (!rc) rc = check_cuda(cudaStreamWaitEvent(*as, p->ev_in[s], 0));
@@ -1641,7 +1644,7 @@ int async_end(sfft4_plan_s* p, cudaStream_t as) {
     const int rc = check_cuda(cudaEventRecord(p->ev_done[s], as));
     if (rc) return rc;
     p->async_used |= 1 << s;
-    p->async_next = s ^ 1;
+    p->async_next = (s + 1) % async_depth(p->grp != nullptr);
     return SFFT4_OK;
 }
 
@@ -1811,7 +1814,7 @@ int sfft4_execute_batched_async(sfft4_plan_t p, int32_t nsig, const void* x_dev,
 
 int sfft4_wait(sfft4_plan_t p, void* stream) {
     if (!p) return SFFT4_EINVAL;
-    for (int s = 0; s < 2; ++s)
+    for (int s = 0; s < kAsyncDepth; ++s)
         if ((p->async_used >> s) & 1) {
             const int rc = check_cuda(cudaStreamWaitEvent((cudaStream_t)stream, p->ev_done[s], 0));
             if (rc) return rc;
@@ -1843,8 +1846,13 @@ int sfft4_bucketize(sfft4_plan_t p, const void* x_dev, int32_t signal, int32_t m
 int sfft4_stats(sfft4_plan_t p, sfft4_run_stats* out) {
     if (!p || !out) return SFFT4_EINVAL;
     memset(out, 0, sizeof(*out));
-    out->executes = p->n_executes + (p->peer ? p->peer->n_executes : 0);
-    out->transforms = p->n_transforms + (p->peer ? p->peer->n_transforms : 0);
+    out->executes = p->n_executes;
+    out->transforms = p->n_transforms;
+    for (const sfft4_plan_s* q : p->peer)
+        if (q) {
+            out->executes += q->n_executes;
+            out->transforms += q->n_transforms;
+        }
     out->last_nsig = p->last_nsig;
     std::vector<FinalJob> jobs;
     if (p->grp) {
@@ -1912,10 +1920,11 @@ int sfft4_sync_status(sfft4_plan_t p) {
 int sfft4_profile_get(sfft4_plan_t p, sfft4_profile* out, int32_t reset) {
     if (!p || !out) return SFFT4_EINVAL;
     if (!p->o.profile) return SFFT4_ESTATE;
-    if (p->peer) {
-        // the second workspace's launches (asynchronous executes) count with this plan's
+    for (sfft4_plan_s* pp : p->peer) {
+        if (!pp) continue;
+        // the other workspaces' launches (asynchronous executes) count with this plan's
         sfft4_profile q;
-        int rc = sfft4_profile_get(p->peer, &q, 1);
+        int rc = sfft4_profile_get(pp, &q, 1);
         if (rc) return rc;
         p->prof_tot.fold_launches += q.fold_launches;
         p->prof_tot.fold_ms += q.fold_ms;

@@ -134,12 +134,12 @@ void free_plan(sfft4_plan_s* p) {
     for (cudaEvent_t e : p->ev)
         if (e) cudaEventDestroy(e);
     if (p->dstream) cudaStreamDestroy(p->dstream);
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < sfft4::kAsyncDepth; ++s) {
         if (p->ev_in[s]) cudaEventDestroy(p->ev_in[s]);
         if (p->ev_done[s]) cudaEventDestroy(p->ev_done[s]);
         if (p->astream[s]) cudaStreamDestroy(p->astream[s]);
     }
-    free_plan(p->peer);
+    for (sfft4_plan_s* q : p->peer) free_plan(q);
     sfft4::destroy_group(p->grp);
     delete p;
 }

@@ -22,6 +22,12 @@ constexpr int kBMin = 16;
 constexpr int kBMax = 4096;
 constexpr int kKMax = 4096;
 constexpr int kDecodeThreads = 512;     // two decode CTAs per SM
+constexpr int kAsyncDepth = 3;          // most workspaces of the asynchronous executes
+// Batches in flight: two for a uniform batch (a third would run two signal-major folds at
+// once and spoil their L2 reuse: 54 K against 79 K transforms/s at N = 2^22, K = 1000), three
+// for a batch of uneven signals (folded level by level; its step is its decode chain, and
+// two chains overlap: 78 K against 66 K transforms/s on the 512-signal workload).
+inline int async_depth(bool uneven) { return uneven ? 3 : 2; }
 constexpr int kFoldSmemMax = 100 * 1024;     // staged window rows of one fold CTA
 
 // Rounds [r0, r0 + nr) of one iteration that one fold launch accumulates, and the
@@ -231,16 +237,17 @@ struct sfft4_plan_s {
     float2* zall = nullptr;     // [sig][ytot] folded arrays of every iteration
     float2* uall = nullptr;     // [sig][ytot] four-step scratch of every iteration (BF16X3)
     std::vector<sfft4::SigFoldHost> sm_fold;  // launches (more than one past kSigJobs jobs)
-    // asynchronous executes (sfft4_execute_batched_async): two workspaces, this plan's and a
-    // peer plan's, used in turn on their own streams; ev_done[s] marks slot s's latest execute
-    sfft4_plan_s* peer = nullptr;
+    // asynchronous executes (sfft4_execute_batched_async): kAsyncDepth workspaces, this
+    // plan's (slot 0) and peer plans' (slots 1..), used in turn on their own streams;
+    // ev_done[s] marks slot s's latest execute
+    sfft4_plan_s* peer[sfft4::kAsyncDepth - 1] = {};
     std::vector<int64_t> bN, bK;        // sfft4_plan_batched's arguments (to make the peer)
     std::vector<int32_t> bB1;
     double bq = 0;
     sfft4_opts bopts;
-    cudaStream_t astream[2] = {nullptr, nullptr};
-    cudaEvent_t ev_in[2] = {nullptr, nullptr};
-    cudaEvent_t ev_done[2] = {nullptr, nullptr};
+    cudaStream_t astream[sfft4::kAsyncDepth] = {};
+    cudaEvent_t ev_in[sfft4::kAsyncDepth] = {};
+    cudaEvent_t ev_done[sfft4::kAsyncDepth] = {};
     int async_next = 0, async_used = 0;
     int32_t* status = nullptr;  // 1 when a bounded device wait gave up
     int sm_count = 0;

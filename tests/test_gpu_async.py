@@ -1,7 +1,8 @@
 """Asynchronous batched executes (sfft4_execute_batched_async / sfft4_wait), on a GB300.
 
-Consecutive asynchronous calls use the plan's two workspaces in turn on the plan's own
-streams, so batch k's decode chain overlaps batch k+1's gather.  Every batch must give,
+Consecutive asynchronous calls use the plan's workspaces in turn (two for a uniform batch,
+three for a batch of uneven signals) on the plan's own streams, so batch k's decode chain
+overlaps batch k+1's gather.  Every batch must give,
 bit for bit, the results of a synchronous execute of the same batch (same kernels, same
 reduction orders), whatever the interleaving: four batches in flight through two
 workspaces, a synchronous execute issued behind asynchronous ones, CUDA-graph replay, and
@@ -109,7 +110,7 @@ def test_async_rejects_trace_plans(s4):
 
 def test_uneven_batch_async_equals_synchronous(s4):
     """Batches of signals of different N and K (sfft4_execute_batched_v_async): three batches
-    of different contents in flight through two workspaces, each bit-identical to a
+    of different contents in flight through three workspaces, each bit-identical to a
     synchronous execute, with and without graph replay."""
     import torch
     from synth.signals import device_signal
