@@ -18,7 +18,7 @@ import parity_helpers as PH
 
 pytestmark = pytest.mark.gpu
 
-CONFIGS = {
+WORKLOADS = {
     # name: (N, K, l, q, B1)
     "c1": (2**14, 16, 4, 0.5, 64),
     "c2": (2**20, 100, 16, 1.0, 128),
@@ -45,7 +45,7 @@ def oracle_plan(N, K, l, q, seed, B1):
 
 @pytest.mark.parametrize("name", ["c1", "c2", "c3"])
 def test_plan_matches_oracle(s4, name):
-    N, K, l, q, B1 = CONFIGS[name]
+    N, K, l, q, B1 = WORKLOADS[name]
     p = s4.Plan(N, K, l, q, seed=3, B1=B1)
     op = oracle_plan(N, K, l, q, 3, B1)
     assert p.info["n_iters"] == len(op.iters)
@@ -63,7 +63,7 @@ def test_plan_matches_oracle(s4, name):
 
 @pytest.mark.parametrize("name", ["c1", "c3"])
 def test_window_tables_match_oracle(s4, name):
-    N, K, l, q, B1 = CONFIGS[name]
+    N, K, l, q, B1 = WORKLOADS[name]
     p = s4.Plan(N, K, l, q, seed=0, B1=B1)
     for B in sorted({p.iter_info(m)["B"] for m in range(1, p.info["n_iters"] + 1)}):
         G, Gh = p.window(B)
@@ -103,7 +103,7 @@ def bucket_parity(s4, N, K, l, q, B1, seed, snr, ms, signal=0, precision="fp32")
 
 @pytest.mark.parametrize("name,snr,ms", [("c1", None, [1, 2, 5]), ("c2", 20.0, [1, 4]), ("c3", None, [1, 6])])
 def test_bucketize_parity(s4, name, snr, ms):
-    N, K, l, q, B1 = CONFIGS[name]
+    N, K, l, q, B1 = WORKLOADS[name]
     bucket_parity(s4, N, K, l, q, B1, seed=11, snr=snr, ms=ms)
 
 
@@ -111,13 +111,13 @@ def test_bucketize_parity(s4, name, snr, ms):
 def test_bucketize_parity_bf16x3(s4, name, snr, ms):
     """The tensor-core BF16x3 split DFT keeps the bucket arrays within the FP32 bound of
     the FP64 oracle (single-stage B <= 64 and four-step B > 64 both covered)."""
-    N, K, l, q, B1 = CONFIGS[name]
+    N, K, l, q, B1 = WORKLOADS[name]
     bucket_parity(s4, N, K, l, q, B1, seed=11, snr=snr, ms=ms, precision="bf16x3")
 
 
 def test_bf16x3_matches_fp32_dft(s4):
     """Every bucket count of the schedule: the tensor-core DFT agrees with the FP32 FFT."""
-    N, K, l, q, B1 = CONFIGS["c3"]
+    N, K, l, q, B1 = WORKLOADS["c3"]
     sig = sparse_signal(N, K, 2, None)
     xd = to_dev(sig.x)
     pf = s4.Plan(N, K, l, q, seed=2, B1=B1)
@@ -138,12 +138,12 @@ def test_bf16x3_matches_fp32_dft(s4):
 
 
 def test_bucketize_parity_other_signal_index(s4):
-    N, K, l, q, B1 = CONFIGS["c2"]
+    N, K, l, q, B1 = WORKLOADS["c2"]
     bucket_parity(s4, N, K, l, q, B1, seed=5, snr=None, ms=[1], signal=37)
 
 
 def e2e(s4, name, seed, snr=None, trace=False, precision="fp32"):
-    N, K, l, q, B1 = CONFIGS[name]
+    N, K, l, q, B1 = WORKLOADS[name]
     sig = sparse_signal(N, K, seed, snr)
     p = s4.Plan(N, K, l, q, seed=seed, B1=B1, trace=trace, precision=precision)
     idx, val, nf, votes = p.execute(to_dev(sig.x))
@@ -154,7 +154,7 @@ def e2e(s4, name, seed, snr=None, trace=False, precision="fp32"):
 
 
 def explain_divergence(p, r, name, seed):
-    N, K, l, q, B1 = CONFIGS[name]
+    N, K, l, q, B1 = WORKLOADS[name]
     return PH.explain_divergence(p, r, N, K, l, q, seed, B1)
 
 
@@ -171,7 +171,7 @@ def test_end_to_end_noiseless(s4, name, seeds, precision):
             assert explain_divergence(p, r, name, seed) is not None
         rel = np.linalg.norm(v - r["v"]) / np.linalg.norm(r["v"])
         assert rel <= 1e-5, (seed, rel)
-        K = CONFIGS[name][1]
+        K = WORKLOADS[name][1]
         assert np.all(idx_all[len(f):] == -1) and np.all(val_all[len(f):] == 0)
         assert len(f) == K
         p.close()
@@ -195,7 +195,7 @@ def test_replay_decode_parity(s4, name, seed, snr):
     """Each iteration's decode (update, selection, location, votes, estimate, merge) of the
     oracle, fed the GPU's own raw bucket arrays and found set, reproduces the GPU's found set:
     frequencies and votes exactly (except decisions within a fragile margin), values 1e-4."""
-    N, K, l, q, B1 = CONFIGS[name]
+    N, K, l, q, B1 = WORKLOADS[name]
     sig = sparse_signal(N, K, seed, snr)
     p = s4.Plan(N, K, l, q, seed=seed, B1=B1, trace=True)
     p.execute(to_dev(sig.x))
@@ -229,7 +229,7 @@ def test_replay_decode_parity(s4, name, seed, snr):
 
 def test_batched_matches_single_and_oracle(s4):
     import torch
-    N, K, l, q, B1 = CONFIGS["c2"]
+    N, K, l, q, B1 = WORKLOADS["c2"]
     seed = 4
     sigs = [sparse_signal(N, K, 100 + i, None) for i in range(3)]
     xs = torch.stack([to_dev(s.x) for s in sigs])
@@ -250,7 +250,7 @@ def test_batched_matches_single_and_oracle(s4):
 
 def test_repeat_runs_bit_identical(s4):
     import torch
-    N, K, l, q, B1 = CONFIGS["c2"]
+    N, K, l, q, B1 = WORKLOADS["c2"]
     sig = sparse_signal(N, K, 9, 20.0)
     p = s4.Plan(N, K, l, q, seed=9, B1=B1)
     x = to_dev(sig.x)
@@ -263,7 +263,7 @@ def test_repeat_runs_bit_identical(s4):
 
 def test_zero_signal_finds_nothing(s4):
     import torch
-    N, K, l, q, B1 = CONFIGS["c1"]
+    N, K, l, q, B1 = WORKLOADS["c1"]
     p = s4.Plan(N, K, l, q, seed=0, B1=B1)
     idx, val, nf, votes = p.execute(torch.zeros(N, dtype=torch.complex64, device="cuda"))
     assert int(nf) == 0 and torch.all(idx == -1)
@@ -291,7 +291,7 @@ def test_stats_counts_and_votes_histogram(s4):
     last execute's found sets that agrees with the votes the execute returned (noiseless:
     the found sets hold exactly the K true frequencies)."""
     import torch
-    N, K, l, q, B1 = CONFIGS["c2"]
+    N, K, l, q, B1 = WORKLOADS["c2"]
     sigs = [sparse_signal(N, K, 200 + i, None) for i in range(3)]
     xs = torch.stack([to_dev(s.x) for s in sigs])
     p = s4.Plan(N, K, l, q, seed=7, B1=B1, max_batch=4)

@@ -84,7 +84,7 @@ def test_window_spectrum_matches_direct_sum():
     assert np.max(np.abs(d.real - full[ks])) < 1e-13
 
 
-def test_window_halfwidth_matches_survey_shape():
+def test_window_halfwidth_is_about_44_buckets():
     # w ~ 44.3 B at delta = 1e-8 (Gaussian tail truncated at delta)
     for B in (16, 64, 1024, 4096):
         h, _ = P.window_halfwidth(2**26, B, 1e-8)
