@@ -648,10 +648,11 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig) 
     // of every round r.  Contributions accumulate in int64 fixed point (2^(fx-40) units,
     // fx = exponent of the largest bucket of iteration 1), so the sum does not depend on the
     // order of the additions.  Gather form: the found entries (v, f and G'^ for their three
-    // buckets) are staged in shared memory in bucket order; per pass of kUpdRounds rounds the
-    // rotated values v e^{2 pi i f o_r / N} are computed once per entry, then each (bucket b',
-    // split) work item sums the entries of b'-1, b', b'+1 in registers; with several splits
-    // per bucket (B < block size) the partial sums are added in a fixed order.  For
+    // buckets) are staged in shared memory in bucket order, stably (found-set order within a
+    // bucket); per pass of kUpdRounds rounds the rotated values v e^{2 pi i f o_r / N} are
+    // computed once per entry, then each (bucket b', split) work item sums the entries of
+    // b'-1, b', b'+1 in FP32 in that fixed order and converts the sum once; with several
+    // splits per bucket (B < block size) the items' int64 sums are added in a fixed order.  For
     // B > kGatherMaxB, or when the staged entries do not fit in shared memory, the entries
     // scatter their contributions with integer atomics into warp-private accumulator copies
     // instead (the same integer sums).
@@ -703,25 +704,47 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig) 
                 if (tid == 0) cnt[B] = tot;
             }
             __syncthreads();
-            for (int e = tid; e < F0; e += T) {
-                const uint32_t f = (uint32_t)ff[e];
-                const double2 vd = fv[e];
-                const uint32_t u = (sigma * f) & mask;
-                const int b0 = (int)(((u + (L >> 1)) >> logL) & (uint32_t)(B - 1));
-                float g3[3];
+            // stable placement: within a bucket, entries keep their found-set order (ranks from
+            // warp matches, the warps of a chunk taking their turn in order), so that each item
+            // below adds its entries in a fixed order
+            const int lane = tid & 31, wid = tid >> 5, nw = (T + 31) >> 5;
+            for (int c0 = 0; c0 < F0; c0 += T) {
+                const int e = c0 + tid;
+                const bool has = e < F0;
+                uint32_t f = 0;
+                float2 ve = make_float2(0.f, 0.f);
+                int b0 = B + lane;  // a key of its own for lanes without an entry
+                float g3[3] = {0.f, 0.f, 0.f};
+                if (has) {
+                    f = (uint32_t)ff[e];
+                    const double2 vd = fv[e];
+                    ve = make_float2((float)vd.x, (float)vd.y);
+                    const uint32_t u = (sigma * f) & mask;
+                    b0 = (int)(((u + (L >> 1)) >> logL) & (uint32_t)(B - 1));
 #pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    const int bb = (b0 + q - 1) & (B - 1);
-                    const int k = (int)((((uint32_t)bb * L - u) + halfN) & mask) - (int)halfN;
-                    g3[q] = it->Ghat[k < 0 ? -k : k] * scale;
+                    for (int q = 0; q < 3; ++q) {
+                        const int bb = (b0 + q - 1) & (B - 1);
+                        const int k = (int)((((uint32_t)bb * L - u) + halfN) & mask) - (int)halfN;
+                        g3[q] = it->Ghat[k < 0 ? -k : k] * scale;
+                    }
                 }
-                const int pos = atomicAdd(&fillp[b0], 1);
-                ev[pos] = make_float2((float)vd.x, (float)vd.y);
-                ef[pos] = f;
+                const unsigned grp = __match_any_sync(0xffffffffu, b0);
+                const int rank = __popc(grp & ((1u << lane) - 1u));
+                for (int w = 0; w < nw; ++w) {
+                    if (wid == w) {
+                        if (has) {
+                            const int pos = fillp[b0] + rank;
+                            ev[pos] = ve;
+                            ef[pos] = f;
 #pragma unroll
-                for (int q = 0; q < 3; ++q) eg[3 * pos + q] = g3[q];
+                            for (int q = 0; q < 3; ++q) eg[3 * pos + q] = g3[q];
+                        }
+                        __syncwarp();
+                        if (has && rank == 0) fillp[b0] += __popc(grp);
+                    }
+                    __syncthreads();
+                }
             }
-            __syncthreads();
             for (int r0 = 0; r0 < R; r0 += kUpdRounds) {
                 const int nr = min(kUpdRounds, R - r0);
                 // round-major (ec[rr F0 + j]): the entries a warp gathers below fall in
@@ -740,9 +763,11 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig) 
                 __syncthreads();
                 for (int item = tid; item < B * splits; item += T) {
                     const int bp = item % B, sp = item / B;
-                    long long ar[kUpdRounds], ai[kUpdRounds];
+                    // the item's few entries add in FP32 in their staged (fixed) order; the
+                    // items' sums then add exactly in int64
+                    float fr[kUpdRounds], fi[kUpdRounds];
 #pragma unroll
-                    for (int rr = 0; rr < kUpdRounds; ++rr) ar[rr] = ai[rr] = 0;
+                    for (int rr = 0; rr < kUpdRounds; ++rr) fr[rr] = fi[rr] = 0.f;
 #pragma unroll
                     for (int q = -1; q <= 1; ++q) {
                         // entries of bucket bp + q reach bp with their G'^ at offset -q
@@ -754,11 +779,17 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig) 
                             for (int rr = 0; rr < kUpdRounds; ++rr) {
                                 if (rr < nr) {
                                     const float2 c = ec[rr * F0 + j];
-                                    ar[rr] += f2ll_rn(g * c.x);
-                                    ai[rr] += f2ll_rn(g * c.y);
+                                    fr[rr] = fmaf(g, c.x, fr[rr]);
+                                    fi[rr] = fmaf(g, c.y, fi[rr]);
                                 }
                             }
                         }
+                    }
+                    long long ar[kUpdRounds], ai[kUpdRounds];
+#pragma unroll
+                    for (int rr = 0; rr < kUpdRounds; ++rr) {
+                        ar[rr] = f2ll_rn(fr[rr]);
+                        ai[rr] = f2ll_rn(fi[rr]);
                     }
                     if (splits == 1) {
 #pragma unroll
