@@ -157,8 +157,9 @@ def measured_peaks():
 
 def fold_source_sha256():
     """sha256 of what sets the fold's DRAM traffic: kernels.cu from its fold section header
-    up to the FFT section header, the signal-major launch builder, and plan.cu (residue
-    slices, copies, fold groups and the L2 fetch granularity)."""
+    up to the FFT section header and the signal-major launch builder; from plan.cu the round
+    segments (build_group), the fold groups, residue slices and copies of each iteration, and
+    the lines that set the L2 fetch granularity."""
     csrc = os.path.join(ROOT, "paper_2011_05698_gb300", "csrc")
     src = open(os.path.join(csrc, "kernels.cu")).read()
     a = src.index("// ----------------------------------------------------------------- fold")
@@ -166,7 +167,12 @@ def fold_source_sha256():
     c = src.index("int build_signal_major_fold(")
     d = src.index("int launch_fft_multi(")
     plan = open(os.path.join(csrc, "plan.cu")).read()
-    return hashlib.sha256((src[a:b] + src[c:d] + plan).encode()).hexdigest()
+    e = plan.index("void build_group(")
+    f = plan.index("\n}\n", e)
+    g = plan.index("// fold groups of up to kFoldRG rounds")
+    h = plan.index("p->samples += ih.unique;", g)
+    fetch = "".join(ln for ln in plan.splitlines(True) if "L2Fetch" in ln or "l2_fetch_bytes" in ln)
+    return hashlib.sha256((src[a:b] + src[c:d] + plan[e:f] + plan[g:h] + fetch).encode()).hexdigest()
 
 
 def fold_traffic_record():
