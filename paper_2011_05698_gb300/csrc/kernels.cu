@@ -1870,6 +1870,8 @@ int sfft4_bucketize(sfft4_plan_t p, const void* x_dev, int32_t signal, int32_t m
     if (!p || !x_dev || !y_dev || signal < 0 || m < 1 || m > (int32_t)p->iters.size())
         return p && p->grp ? SFFT4_ESTATE : SFFT4_EINVAL;
     const IterDev& d = p->iters[m - 1].d;
+    const int rc = join_slot0(p, (cudaStream_t)stream);  // the plan's own workspace
+    if (rc) return rc;
     return launch_bucketize(p, m - 1, 1, (const float2*)x_dev, p->N, signal, (float2*)y_dev,
                             (int64_t)d.R * d.B, (cudaStream_t)stream);
 }
