@@ -139,6 +139,37 @@ def test_bucketize_lemma1_identity(N, B):
             assert abs(Y[s, b] - expect) < 1e-10 * max(1.0, abs(expect))
 
 
+@pytest.mark.parametrize("N,B,K", [(2**12, 32, 6), (2**14, 64, 12)])
+def test_update_removes_exact_coefficients(N, B, K):
+    """Reading R13: subtracting the true coefficients of a noiseless K-sparse signal from
+    buckets b-1, b, b+1 of every round (G'^_{b'L-u} v e^{2 pi i f o / N}) leaves only the
+    window's leakage beyond the neighbours (each |G'^_k| <= delta there).  A wrong phase sign,
+    a missing neighbour bucket or a wrong round offset leaves residuals of the buckets' own
+    size; with half of the coefficients removed, the other half must remain untouched."""
+    sig = sparse_signal(N, K, 3, None)
+    x = sig.x.astype(np.complex128)
+    L = N // B
+    G, h, Ghat = W.WindowCache(N, 1e-8).get(B)
+    sigma, a = 2 * 83 + 1, 1234 % N
+    offs = [(a + sigma * t) % N for t in (0, 7, 301, 4099 % N)]
+    Y = sfft4.bucketize(x, N, B, G, h, sigma, offs)
+    scale = np.max(np.abs(Y))
+    full = sfft4.FoundSet()
+    for f, v in zip(sig.freqs, sig.values):
+        full.merge(int(f), complex(v), 0, 1)
+    assert np.max(np.abs(sfft4.update(Y, full, N, B, L, sigma, offs, Ghat))) <= 1e-6 * scale
+    # removing half of the coefficients equals the bucketization of the other half alone
+    half = sfft4.FoundSet()
+    for f, v in list(zip(sig.freqs, sig.values))[: K // 2]:
+        half.merge(int(f), complex(v), 0, 1)
+    rest = np.zeros(N, dtype=np.complex128)
+    n = np.arange(N)
+    for f, v in list(zip(sig.freqs, sig.values))[K // 2:]:
+        rest += v * np.exp(2j * np.pi * ((f * n) % N) / N)
+    Yrest = sfft4.bucketize(rest, N, B, G, h, sigma, offs)
+    assert np.max(np.abs(sfft4.update(Y, half, N, B, L, sigma, offs, Ghat) - Yrest)) <= 1e-6 * scale
+
+
 def test_unique_samples_counts_union():
     it = P.make_iteration(1, 2**22, 22, 1024, 16, 256, 1e-8)
     brute = set()
