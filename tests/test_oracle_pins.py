@@ -170,6 +170,43 @@ def test_update_removes_exact_coefficients(N, B, K):
     assert np.max(np.abs(sfft4.update(Y, half, N, B, L, sigma, offs, Ghat) - Yrest)) <= 1e-6 * scale
 
 
+@pytest.mark.parametrize("N,B", [(256, 16), (1024, 32), (4096, 256)])
+def test_bucket_of_nearest_centre_ties_up(N, B):
+    """Reading R5: u falls in bucket b when u lies in [(2b-1)L/2, (2b+1)L/2) (mod N), i.e.
+    b L is the nearest bucket centre on the circle and a half-way u goes to the upper
+    bucket.  Checked for every u against a brute-force nearest-centre search."""
+    L = N // B
+    u = np.arange(N, dtype=np.int64)
+    got = sfft4.bucket_of(u, L, B)
+    centres = np.arange(B, dtype=np.int64) * L
+    for uu in range(N):
+        d = (uu - centres) % N
+        d = np.where(d >= N - d, d - N, d)          # signed distance in [-N/2, N/2)
+        best = np.flatnonzero(np.abs(d) == np.abs(d).min())
+        # the nearest centre; at a half-way u the upper bucket (its centre lies above u)
+        want = best[0] if len(best) == 1 else [b for b in best if d[b] < 0][0]
+        assert got[uu] == want, (uu, got[uu], want)
+
+
+def test_select_top_energy_ties_to_lower_bucket():
+    """Reading R11: the candidates are the n_c buckets of largest |yhat_0|^2 (equal keys: the
+    lower bucket first), keeping only those strictly above the floor theta; returned sorted.
+    Checked on keys with planted ties against a brute-force sort."""
+    rng = np.random.default_rng(7)
+    for trial in range(200):
+        B = int(rng.choice([16, 32, 64]))
+        # values with exact squared magnitudes, so that equal keys are exact ties
+        vals = np.array([0, 1, -1, 1j, -1j, 1 + 1j, 2, -2j, 1 - 1j, 0.5, 3j, -1.5 + 2j])
+        Y0 = rng.choice(vals, size=B).astype(np.complex128)
+        key = Y0.real ** 2 + Y0.imag ** 2
+        n_c = int(rng.integers(1, B + 1))
+        theta = float(rng.choice([0.0, 0.2, 1.0, 4.0]))
+        got, _ = sfft4.select(Y0, n_c, theta)
+        order = sorted(range(B), key=lambda b: (-key[b], b))
+        want = sorted(b for b in order[:n_c] if key[b] > theta)
+        assert [int(b) for b in got] == want, (trial, list(got), want)
+
+
 def test_unique_samples_counts_union():
     it = P.make_iteration(1, 2**22, 22, 1024, 16, 256, 1e-8)
     brute = set()
