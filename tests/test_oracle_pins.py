@@ -410,6 +410,27 @@ def test_median_estimate_even_rounds():
     assert v[0] == 2.5 + 0.5j
 
 
+def test_finalize_top_k_ties_to_lower_frequency():
+    """Reading R16: the output is the K entries of largest |v| (equal magnitudes: the lower
+    frequency first), sorted by frequency, with their votes.  Checked on found sets with
+    exact planted ties against a brute-force sort."""
+    rng = np.random.default_rng(11)
+    vals = np.array([1, -1, 1j, 2, -2j, 1 + 1j, 0.5, 3, -3j, 0.25j])
+    for trial in range(200):
+        n = int(rng.integers(1, 40))
+        fs = sfft4.FoundSet()
+        for f in rng.choice(4096, size=n, replace=False):
+            fs.merge(int(f), complex(rng.choice(vals)), int(rng.integers(0, 5)), 1)
+        K = int(rng.integers(1, 50))
+        out = sfft4.finalize(fs, K)
+        entries = sorted(zip(fs.f, fs.v, fs.votes), key=lambda e: (-abs(e[1]), e[0]))[:K]
+        entries.sort(key=lambda e: e[0])
+        assert out["f"].tolist() == [e[0] for e in entries], trial
+        assert out["v"].tolist() == [e[1] for e in entries], trial
+        assert out["votes"].tolist() == [e[2] for e in entries], trial
+        assert out["nfound"] == len(entries)
+
+
 def test_merge_adds_repeated_frequency():
     fs = sfft4.FoundSet()
     fs.merge(5, 1 + 1j, 4, 1)
