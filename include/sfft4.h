@@ -77,7 +77,8 @@ typedef struct {
     int32_t max_batch;       /* most signals one sfft4_execute_batched call may pass;
                                 sizes the workspace; with the signal-major fold, max_batch
                                 x the fold tiles of one signal must stay below 2^31 (one
-                                launch grid), else SFFT4_EINVAL; default 1                  */
+                                launch grid), with the iteration-major fold max_batch <= 65535
+                                (signals in grid.y), else SFFT4_EINVAL; default 1           */
     int32_t trace;           /* nonzero: keep per-iteration bucket arrays and found sets
                                 of signal 0 for sfft4_trace_get (tests); default 0         */
     int32_t profile;         /* nonzero: bracket each kernel launch of an execute with CUDA
@@ -105,6 +106,10 @@ typedef struct {
                                 read from DRAM once and re-read from L2;
                                 SFFT4_FOLD_ITERATION_MAJOR: one launch per iteration group over
                                 the whole batch (each signal's samples read once per iteration) */
+    int32_t trace_signal;    /* with trace: the batch index of the signal whose per-iteration
+                                bucket arrays and found sets sfft4_trace_get returns (0 <=
+                                trace_signal < max_batch; an execute of fewer signals than
+                                trace_signal + 1 returns SFFT4_EINVAL); default 0           */
 } sfft4_opts;
 
 /* Fills *opts with the defaults above.  Returns SFFT4_EINVAL if opts is NULL. */
@@ -133,7 +138,13 @@ SFFT4_API int sfft4_plan(sfft4_plan_t* out, int64_t N, int64_t K, int32_t l, dou
 SFFT4_API void sfft4_destroy(sfft4_plan_t plan);
 
 /*
- * sfft4_execute -- one transform (signal index 0 of the Philox counter).
+ * sfft4_execute -- one transform (signal index 0 of the Philox counter): the problem of
+ * Section 2.1 (from the samples of x, the K largest coefficients X_f of its DFT, Eq. 1-2)
+ * solved by the iterations of Section 3.1 -- per iteration the bucketization of Lemma 1
+ * (random spectral permutation, Eq. 7-8; flat window, Eq. 9-10; fold and B-point DFT, Eq.
+ * 11-13), the update by the coefficients found so far, the multiscale location of the large
+ * buckets (Section 3.2, Eq. 15-19), the estimation of Eq. 14 and the merge x^m = x^{m-1} +
+ * x'^m -- followed by the K-sparse output.
  *   x_dev      N complex64 samples (interleaved re, im float32), device memory, 8-byte aligned
  *   idx_dev    K int64 outputs: frequencies in [0, N) ascending; unused tail = -1
  *   val_dev    K complex128 outputs X_f in the Eq. 2 normalisation; unused tail = 0
@@ -147,8 +158,10 @@ SFFT4_API int sfft4_execute(sfft4_plan_t plan, const void* x_dev, int64_t* idx_d
                   int64_t* nfound_dev, int8_t* votes_dev, void* stream);
 
 /*
- * sfft4_execute_batched -- nsig independent transforms of the plan's (N, K) in one pass
- * of batched kernels; signal i uses Philox counter (i, m, 0, 0).
+ * sfft4_execute_batched -- nsig independent instances of the problem of Section 2.1, each
+ * solved by the iterations of Section 3.1 as in sfft4_execute, in one pass of batched
+ * kernels (every kernel of an iteration covers all signals); signal i uses Philox counter
+ * (i, m, 0, 0).
  *   nsig        1 <= nsig <= opts.max_batch of the plan
  *   x_dev       nsig * x_stride complex64 elements, device; signal i starts at
  *               x_dev + i * x_stride (x_stride >= N, in complex elements)
@@ -161,8 +174,9 @@ SFFT4_API int sfft4_execute_batched(sfft4_plan_t plan, int32_t nsig, const void*
                           int8_t* votes_dev, void* stream);
 
 /*
- * sfft4_execute_batched_async -- sfft4_execute_batched for a pipeline of batches: the
- * transforms of one batch (same arguments and results) run on the plan's own streams after
+ * sfft4_execute_batched_async -- sfft4_execute_batched (Section 2.1's problem for every
+ * signal, by the iterations of Section 3.1) for a pipeline of batches: the transforms of
+ * one batch (same arguments and results) run on the plan's own streams after
  * the work queued on `stream` so far, and `stream` does not wait for them, so consecutive
  * calls overlap (the decode chain of one batch with the gather of the next).  Calls use two
  * workspaces in turn; the first call allocates the second (a plan of the same transform and
@@ -180,7 +194,8 @@ SFFT4_API int sfft4_execute_batched_async(sfft4_plan_t plan, int32_t nsig, const
                                           int64_t* idx_dev, sfft4_c128* val_dev, int64_t* nfound_dev,
                                           int8_t* votes_dev, void* stream);
 
-/* Makes `stream` wait for every asynchronous execute issued so far on the plan.
+/* Makes `stream` wait for every asynchronous execute issued so far on the plan.  Pipeline
+ * control only: the paper has no counterpart.
  * Errors: SFFT4_EINVAL, SFFT4_ECUDA. */
 SFFT4_API int sfft4_wait(sfft4_plan_t plan, void* stream);
 
@@ -203,7 +218,9 @@ SFFT4_API int sfft4_plan_batched(sfft4_plan_t* out, int32_t nsig, const int64_t*
                                  const int32_t* B1, int32_t l, double q, uint64_t seed, const sfft4_opts* opts);
 
 /*
- * sfft4_execute_batched_v -- execute a plan from sfft4_plan_batched.
+ * sfft4_execute_batched_v -- execute a plan from sfft4_plan_batched: for every signal i, the
+ * problem of Section 2.1 for (N[i], K[i]) by the iterations of Section 3.1 on that signal's
+ * own schedule (level m of the execute runs iteration m of every signal that has one).
  *   x_ptrs_dev  device array of nsig device pointers; signal i has N[i] complex64 samples
  *               (8-byte aligned) at x_ptrs_dev[i].  The array is read by the kernels, so its
  *               entries may change between executes (also under opts.graph)
@@ -218,7 +235,8 @@ SFFT4_API int sfft4_execute_batched_v(sfft4_plan_t plan, const void* const* x_pt
                                       void* stream);
 
 /*
- * sfft4_execute_batched_v_async -- sfft4_execute_batched_v as a pipeline of batches, with the
+ * sfft4_execute_batched_v_async -- sfft4_execute_batched_v (Section 2.1's problem per signal,
+ * by the iterations of Section 3.1) as a pipeline of batches, with the
  * rules of sfft4_execute_batched_async, but with three workspaces in turn (the first call
  * makes the other two, plans of the same signals and options), so that the decode chains of
  * two batches overlap; at most three calls are in flight; results complete after sfft4_wait.  The pointer table, the
@@ -323,7 +341,7 @@ SFFT4_API int sfft4_bucketize(sfft4_plan_t plan, const void* x_dev, int32_t sign
 
 /*
  * sfft4_trace_get -- after an execute on a plan made with opts.trace != 0, copies (to host,
- * synchronously) for iteration m of signal 0: the raw R x B bucket arrays (complex64,
+ * synchronously) for iteration m of signal opts.trace_signal: the raw R x B bucket arrays (complex64,
  * y_host may be NULL) and the found set after the iteration: *nfound entries of
  * frequency (f_host, int64), value (v_host, complex128) and votes (votes_host, int8),
  * each of capacity `cap` entries (any of them may be NULL).
@@ -380,8 +398,9 @@ SFFT4_API int sfft4_gather_probe(const void* x_dev, int32_t nsig, int64_t N, int
  * Its only scratch is one static device array of 131072 FP64 values (1 MiB, held by every GPU
  * that loads the library until the process exits), so windows longer than 131072
  * coefficients (B > 2048 at delta = 1e-8) are rejected with SFFT4_EINVAL.  The first call on
- * a device looks up that array's address (cudaGetSymbolAddress) once; make that first call
- * before any stream capture.  All calls share the array: calls that overlap on the GPU (on
+ * a device looks up that array's address (cudaGetSymbolAddress) once per device and CUDA
+ * context (after the device's context is destroyed, e.g. by cudaDeviceReset, the next call
+ * looks it up again); make that first call before any stream capture.  All calls share the array: calls that overlap on the GPU (on
  * different streams, or from different host threads) race and must be serialised by the
  * caller.
  * Errors: SFFT4_EINVAL (sizes, capacities, NULL outputs), SFFT4_ECUDA.
@@ -396,6 +415,14 @@ SFFT4_API int sfft4_window_noalloc(int64_t N, int32_t B, double delta, float* G_
  * Clears the flag.  Errors: SFFT4_EINVAL (NULL plan), SFFT4_ECUDA.
  */
 SFFT4_API int sfft4_sync_status(sfft4_plan_t plan);
+
+/*
+ * sfft4_inject_status -- test hook: sets the plan's device status word to `value` (nonzero:
+ * as a bounded device-side wait does when it gives up), synchronously, so that tests can
+ * check sfft4_sync_status's reporting without making a device wait run out.  The paper has
+ * no counterpart.  Errors: SFFT4_EINVAL (NULL plan), SFFT4_ECUDA.
+ */
+SFFT4_API int sfft4_inject_status(sfft4_plan_t plan, int32_t value);
 
 /* Text of an error code (static storage). */
 SFFT4_API const char* sfft4_strerror(int code);

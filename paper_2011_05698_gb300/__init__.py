@@ -47,7 +47,7 @@ def _stream_ptr(device):
 
 def _opts(B1=0, delta=1e-8, precision="fp32", min_votes=0, select_factor=2.0, sig_floor=1e-10,
           mag_tol=0.5, max_iters=64, max_batch=1, trace=False, profile=False, graph=False,
-          location="multiscale", fold_order="signal_major", l2_fetch_bytes=0):
+          location="multiscale", fold_order="signal_major", l2_fetch_bytes=0, trace_signal=0):
     o = _lib.Opts()
     check(_lib.load().sfft4_opts_default(ctypes.byref(o)), "sfft4_opts_default")
     o.B1 = B1
@@ -66,6 +66,7 @@ def _opts(B1=0, delta=1e-8, precision="fp32", min_votes=0, select_factor=2.0, si
     o.fold_order = {"signal_major": _lib.SFFT4_FOLD_SIGNAL_MAJOR,
                     "iteration_major": _lib.SFFT4_FOLD_ITERATION_MAJOR}[fold_order]
     o.l2_fetch_bytes = l2_fetch_bytes
+    o.trace_signal = trace_signal
     return o
 
 
@@ -85,12 +86,12 @@ class Plan:
     def __init__(self, N, K, l=16, q=1.0, seed=0, *, B1=0, delta=1e-8, precision="fp32",
                  min_votes=0, select_factor=2.0, sig_floor=1e-10, mag_tol=0.5, max_iters=64,
                  max_batch=1, trace=False, profile=False, graph=False, location="multiscale",
-                 fold_order="signal_major", l2_fetch_bytes=0, device=None):
+                 fold_order="signal_major", l2_fetch_bytes=0, trace_signal=0, device=None):
         import torch
         lib = _lib.load()
         self.device = _device(device)
         o = _opts(B1, delta, precision, min_votes, select_factor, sig_floor, mag_tol, max_iters,
-                  max_batch, trace, profile, graph, location, fold_order, l2_fetch_bytes)
+                  max_batch, trace, profile, graph, location, fold_order, l2_fetch_bytes, trace_signal)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             check(lib.sfft4_plan(ctypes.byref(h), N, K, l, q, seed, ctypes.byref(o)), "sfft4_plan")
@@ -149,6 +150,10 @@ class Plan:
     def sync_status(self):
         """Synchronise and raise if a bounded device wait of this plan gave up."""
         check(_lib.load().sfft4_sync_status(self._h), "sfft4_sync_status")
+
+    def inject_status(self, value=1):
+        """Test hook: set the plan's device status word as a bounded wait that gave up does."""
+        check(_lib.load().sfft4_inject_status(self._h, value), "sfft4_inject_status")
 
     def stats(self):
         """Counters and the votes histogram of the last execute's found sets (synchronises)."""
@@ -224,7 +229,7 @@ class Plan:
 
     def trace(self, m):
         """(raw buckets (R, B) complex64, found f, found v, found votes) after iteration m
-        of signal 0 of the last execute (plan made with trace=True)."""
+        of the traced signal (trace_signal, default 0) of the last execute (trace=True)."""
         import numpy as np
         it = self.iter_info(m)
         cap = self.info["found_capacity"]

@@ -28,7 +28,7 @@ class Opts(ctypes.Structure):
                 ("max_iters", ctypes.c_int32), ("max_batch", ctypes.c_int32),
                 ("trace", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("l2_fetch_bytes", ctypes.c_int32), ("graph", ctypes.c_int32), ("location", ctypes.c_int32),
-                ("fold_order", ctypes.c_int32)]
+                ("fold_order", ctypes.c_int32), ("trace_signal", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -102,6 +102,7 @@ SIGNATURES = [
     ("sfft4_window_noalloc", ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_double, _P,
                                             ctypes.c_int64, _P, ctypes.c_int64, _P]),
     ("sfft4_sync_status", ctypes.c_int, [_P]),
+    ("sfft4_inject_status", ctypes.c_int, [_P, ctypes.c_int32]),
     ("sfft4_stats", ctypes.c_int, [_P, ctypes.POINTER(RunStats)]),
     ("sfft4_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("sfft4_last_cuda_error", ctypes.c_char_p, []),

@@ -43,6 +43,20 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
+// Polls the mbarrier at shared address `bar` for the completion of phase `parity`, at most
+// `limit` times; returns 1 once it completed, 0 if the wait gave up.
+__device__ __forceinline__ uint32_t mbar_wait_bounded(uint32_t bar, uint32_t parity, uint32_t limit) {
+    uint32_t done = 0;
+    for (uint32_t it = 0; it < limit && !done; ++it) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity));
+    }
+    return done;
+}
+
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
     uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
     d |= (uint64_t)(128u >> 4) << 16;    // leading-byte offset: next core matrix along K
@@ -299,23 +313,12 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_dft_bf16x3(const __grid_cons
             }
             cur = gi;
             dft_store_x(g, tid, val, sX);
-            uint32_t adone = 0;
-            for (uint32_t it = 0; it < kWaitLimit && !adone; ++it) {
-                asm volatile(
-                    "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                    " selp.u32 %0, 1, 0, p;\n}"
-                    : "=r"(adone)
-                    : "r"(smem_u32(&abar)), "r"(aphase));
-            }
+            const uint32_t adone = mbar_wait_bounded(smem_u32(&abar), aphase, kWaitLimit);
             if (!__syncthreads_and(adone)) {
-                // give the copy in flight one more bounded wait before leaving
+                // give up: report, then give the bulk copy still in flight one more bounded wait
+                // before the CTA leaves (no MMA of this tile has been issued)
                 if (tid == 0) atomicExch(L.status, 1);
-                for (uint32_t it = 0, d2 = 0; it < kWaitLimit && !d2; ++it)
-                    asm volatile(
-                        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                        " selp.u32 %0, 1, 0, p;\n}"
-                        : "=r"(d2)
-                        : "r"(smem_u32(&abar)), "r"(aphase));
+                mbar_wait_bounded(smem_u32(&abar), aphase, kWaitLimit);
                 break;
             }
             aphase ^= 1u;
@@ -352,19 +355,17 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_dft_bf16x3(const __grid_cons
         const int gn = (ti + 1 < t_hi) ? group_of(L, ti + 1) : gi;
         if (ti + 1 < t_hi) dft_gather(L.g[gn], ti + 1, tid, val);
         // ---- bounded wait for the accumulator -------------------------------------------
-        uint32_t done = 0;
-        for (uint32_t it = 0; it < kWaitLimit && !done; ++it) {
-            asm volatile(
-                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                " selp.u32 %0, 1, 0, p;\n}"
-                : "=r"(done)
-                : "r"(smem_u32(&mbar)), "r"(phase));
-        }
-        phase ^= 1u;
+        const uint32_t done = mbar_wait_bounded(smem_u32(&mbar), phase, kWaitLimit);
         if (!__syncthreads_and(done)) {
+            // give up: report, then wait once more (bounded) for the commit of this tile's MMAs,
+            // which still write the accumulator, before its TMEM columns are freed below.  If
+            // that wait gives up too the columns are freed regardless: a CTA must not exit
+            // holding tensor memory.
             if (tid == 0) atomicExch(L.status, 1);
+            mbar_wait_bounded(smem_u32(&mbar), phase, kWaitLimit);
             break;
         }
+        phase ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;");
         // ---- epilogue: TMEM rows -> shared stage (row stride kNT + 1) -> complex outputs -
         float* stg = (float*)sX;  // the X pieces are free once the MMAs completed

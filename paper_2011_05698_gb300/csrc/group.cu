@@ -391,6 +391,7 @@ int sfft4_execute_batched_v(sfft4_plan_t p, const void* const* x_ptrs_dev, int64
                              (uint64_t)(uintptr_t)val_dev, (uint64_t)(uintptr_t)nfound_dev,
                              (uint64_t)(uintptr_t)votes_dev, 0, 0};
     int rc = graph_run(p, key, (cudaStream_t)stream, group_body, &r);
+    if (!rc) rc = mark_sync(p, (cudaStream_t)stream);
     if (!rc) {
         p->executed = true;
         ++p->n_executes;

@@ -16,6 +16,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 
 #include "sfft4_internal.cuh"
 
@@ -144,21 +146,8 @@ __global__ void k_twiddles(float2* tw, int B) {
 
 int build_window_tables(sfft4_plan_s* p, Window* w, double delta) {
     int64_t N = p->N, L = w->L, h = w->h, wlen = 2 * h + 1;
-    double c = 0;
-    {
-        // same construction as the planner: s_t = B * 4 sqrt2 erfcinv(delta) / (2 pi)
-        double y = delta;
-        double x = sqrt(-log(y));
-        for (int i = 0; i < 100; ++i) {
-            double f = erfc(x) - y;
-            double d = -2.0 / sqrt(M_PI) * exp(-x * x);
-            double step = f / d;
-            x -= step;
-            if (fabs(step) <= 1e-17 * fabs(x)) break;
-        }
-        c = 4.0 * sqrt(2.0) * x;
-    }
-    double s_t = (double)w->B * c / (2.0 * M_PI);
+    double s_t = 0.0;
+    if (window_halfwidth(w->B, delta, &s_t) != h) return SFFT4_EINVAL;  // the planner's h
     int64_t M = (3 * L) / 4;
     double* g64 = nullptr;
     int rc = check_cuda(cudaMalloc(&g64, wlen * sizeof(double)));
@@ -1588,13 +1577,20 @@ int prof_end(sfft4_plan_s* p, cudaStream_t st, cudaEvent_t a, int kind, int64_t 
     return SFFT4_OK;
 }
 
+// Per device, once: the dynamic shared-memory limits of every kernel.  Host threads may make
+// their first execute on a device at the same time, so the flag is atomic and the set-up runs
+// under a mutex (a failed set-up is retried by the next call).
+static std::atomic<bool> g_configured[64];
+static std::mutex g_configure_mu;
+
 int configure_kernels() {
-    static bool done[64] = {false};
     int dev = 0;
     int rc0 = check_cuda(cudaGetDevice(&dev));
     if (rc0) return rc0;
     if (dev < 0 || dev >= 64) return SFFT4_ECUDA;
-    if (done[dev]) return SFFT4_OK;
+    if (g_configured[dev].load(std::memory_order_acquire)) return SFFT4_OK;
+    std::lock_guard<std::mutex> lk(g_configure_mu);
+    if (g_configured[dev].load(std::memory_order_relaxed)) return SFFT4_OK;
     int rc = SFFT4_OK;
     const void* folds[] = {(const void*)k_fold<1>, (const void*)k_fold<2>, (const void*)k_fold<3>,
                            (const void*)k_fold<4>, (const void*)k_fold<5>, (const void*)k_fold<6>,
@@ -1629,12 +1625,22 @@ int configure_kernels() {
     if (!rc) rc = check_cuda(cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   8 * kKMax));
     if (!rc) rc = configure_dft_tc();
-    if (!rc) done[dev] = true;
+    if (!rc) g_configured[dev].store(true, std::memory_order_release);
     return rc;
 }
 
 int join_slot0(sfft4_plan_s* p, cudaStream_t st) {
     return (p->async_used & 1) ? check_cuda(cudaStreamWaitEvent(st, p->ev_done[0], 0)) : SFFT4_OK;
+}
+
+int mark_sync(sfft4_plan_s* p, cudaStream_t st) {
+    if (!p->ev_sync) {
+        const int rc = check_cuda(cudaEventCreateWithFlags(&p->ev_sync, cudaEventDisableTiming));
+        if (rc) return rc;
+    }
+    const int rc = check_cuda(cudaEventRecord(p->ev_sync, st));
+    if (!rc) p->sync_pending = true;
+    return rc;
 }
 
 // async_depth workspaces used in turn: this plan's (slot 0) and peer plans of the same
@@ -1667,6 +1673,9 @@ int async_begin(sfft4_plan_s* p, cudaStream_t caller, sfft4_plan_s** w, cudaStre
     *as = p->astream[s];
     rc = check_cuda(cudaEventRecord(p->ev_in[s], caller));
     if (!rc) rc = check_cuda(cudaStreamWaitEvent(*as, p->ev_in[s], 0));
+    // slot 0 is the plan's own workspace: also wait for the latest synchronous execute on it,
+    // which may have been issued on another stream than `caller`
+    if (!rc && s == 0 && p->sync_pending) rc = check_cuda(cudaStreamWaitEvent(*as, p->ev_sync, 0));
     return rc;
 }
 
@@ -1776,20 +1785,21 @@ int run_body(sfft4_plan_s* p, const void* ctx, cudaStream_t st) {
             if (rc) return rc;
         }
         const IterDev& d = p->iters[mi].d;
+        const int64_t ts = p->o.trace_signal;  // the traced signal's workspace blocks
         if (p->o.trace) {
-            rc = check_cuda(cudaMemcpyAsync(p->trace_y + mi * rb, ym, (size_t)d.R * d.B * sizeof(float2),
+            rc = check_cuda(cudaMemcpyAsync(p->trace_y + mi * rb, ym + ts * p->ytot, (size_t)d.R * d.B * sizeof(float2),
                                             cudaMemcpyDeviceToDevice, ds));
             if (rc) return rc;
         }
         rc = launch_decode(p, (int)mi, nsig, ds);
         if (rc) return rc;
         if (p->o.trace) {
-            rc = check_cuda(cudaMemcpyAsync(p->trace_F + mi, p->F, sizeof(int32_t), cudaMemcpyDeviceToDevice, ds));
-            if (!rc) rc = check_cuda(cudaMemcpyAsync(p->trace_ff + mi * p->Fcap, p->ff, p->Fcap * sizeof(int32_t),
-                                                     cudaMemcpyDeviceToDevice, ds));
-            if (!rc) rc = check_cuda(cudaMemcpyAsync(p->trace_fv + mi * p->Fcap, p->fv, p->Fcap * sizeof(double2),
-                                                     cudaMemcpyDeviceToDevice, ds));
-            if (!rc) rc = check_cuda(cudaMemcpyAsync(p->trace_votes + mi * p->Fcap, p->fvotes, p->Fcap,
+            rc = check_cuda(cudaMemcpyAsync(p->trace_F + mi, p->F + ts, sizeof(int32_t), cudaMemcpyDeviceToDevice, ds));
+            if (!rc) rc = check_cuda(cudaMemcpyAsync(p->trace_ff + mi * p->Fcap, p->ff + ts * p->Fcap,
+                                                     p->Fcap * sizeof(int32_t), cudaMemcpyDeviceToDevice, ds));
+            if (!rc) rc = check_cuda(cudaMemcpyAsync(p->trace_fv + mi * p->Fcap, p->fv + ts * p->Fcap,
+                                                     p->Fcap * sizeof(double2), cudaMemcpyDeviceToDevice, ds));
+            if (!rc) rc = check_cuda(cudaMemcpyAsync(p->trace_votes + mi * p->Fcap, p->fvotes + ts * p->Fcap, p->Fcap,
                                                      cudaMemcpyDeviceToDevice, ds));
             if (rc) return rc;
         }
@@ -1803,6 +1813,7 @@ int run_body(sfft4_plan_s* p, const void* ctx, cudaStream_t st) {
 int run(sfft4_plan_s* p, int nsig, const float2* x, int64_t x_stride, int64_t* idx,
         sfft4_c128* val, int64_t* nfound, int8_t* votes, cudaStream_t st) {
     if (p->grp) return SFFT4_ESTATE;
+    if (p->o.trace && p->o.trace_signal >= nsig) return SFFT4_EINVAL;
     const RunArgs r{nsig, x, x_stride, idx, val, nfound, votes};
     const uint64_t key[8] = {1, (uint64_t)nsig, (uint64_t)(uintptr_t)x, (uint64_t)x_stride,
                              (uint64_t)(uintptr_t)idx, (uint64_t)(uintptr_t)val,
@@ -1824,9 +1835,10 @@ int sfft4_execute(sfft4_plan_t p, const void* x_dev, int64_t* idx_dev, sfft4_c12
                   int64_t* nfound_dev, int8_t* votes_dev, void* stream) {
     if (!p || !x_dev || !idx_dev || !val_dev || !nfound_dev) return SFFT4_EINVAL;
     int rc = join_slot0(p, (cudaStream_t)stream);
-    if (rc) return rc;
-    return run(p, 1, (const float2*)x_dev, p->N, idx_dev, val_dev, nfound_dev, votes_dev,
-               (cudaStream_t)stream);
+    if (!rc) rc = run(p, 1, (const float2*)x_dev, p->N, idx_dev, val_dev, nfound_dev, votes_dev,
+                      (cudaStream_t)stream);
+    if (!rc) rc = mark_sync(p, (cudaStream_t)stream);
+    return rc;
 }
 
 int sfft4_execute_batched_async(sfft4_plan_t p, int32_t nsig, const void* x_dev, int64_t x_stride,
@@ -1860,9 +1872,10 @@ int sfft4_execute_batched(sfft4_plan_t p, int32_t nsig, const void* x_dev, int64
     if (p->grp) return SFFT4_ESTATE;
     if (nsig < 1 || nsig > p->o.max_batch || x_stride < p->N) return SFFT4_EINVAL;
     int rc = join_slot0(p, (cudaStream_t)stream);
-    if (rc) return rc;
-    return run(p, nsig, (const float2*)x_dev, x_stride, idx_dev, val_dev, nfound_dev, votes_dev,
-               (cudaStream_t)stream);
+    if (!rc) rc = run(p, nsig, (const float2*)x_dev, x_stride, idx_dev, val_dev, nfound_dev, votes_dev,
+                      (cudaStream_t)stream);
+    if (!rc) rc = mark_sync(p, (cudaStream_t)stream);
+    return rc;
 }
 
 int sfft4_bucketize(sfft4_plan_t p, const void* x_dev, int32_t signal, int32_t m, void* y_dev,
@@ -1870,10 +1883,11 @@ int sfft4_bucketize(sfft4_plan_t p, const void* x_dev, int32_t signal, int32_t m
     if (!p || !x_dev || !y_dev || signal < 0 || m < 1 || m > (int32_t)p->iters.size())
         return p && p->grp ? SFFT4_ESTATE : SFFT4_EINVAL;
     const IterDev& d = p->iters[m - 1].d;
-    const int rc = join_slot0(p, (cudaStream_t)stream);  // the plan's own workspace
-    if (rc) return rc;
-    return launch_bucketize(p, m - 1, 1, (const float2*)x_dev, p->N, signal, (float2*)y_dev,
-                            (int64_t)d.R * d.B, (cudaStream_t)stream);
+    int rc = join_slot0(p, (cudaStream_t)stream);  // the plan's own workspace
+    if (!rc) rc = launch_bucketize(p, m - 1, 1, (const float2*)x_dev, p->N, signal, (float2*)y_dev,
+                                   (int64_t)d.R * d.B, (cudaStream_t)stream);
+    if (!rc) rc = mark_sync(p, (cudaStream_t)stream);
+    return rc;
 }
 
 int sfft4_stats(sfft4_plan_t p, sfft4_run_stats* out) {
@@ -1948,6 +1962,11 @@ int sfft4_sync_status(sfft4_plan_t p) {
         return SFFT4_ETIMEOUT;
     }
     return SFFT4_OK;
+}
+
+int sfft4_inject_status(sfft4_plan_t p, int32_t value) {
+    if (!p || !p->status) return SFFT4_EINVAL;
+    return check_cuda(cudaMemcpy(p->status, &value, sizeof(int32_t), cudaMemcpyHostToDevice));
 }
 
 int sfft4_profile_get(sfft4_plan_t p, sfft4_profile* out, int32_t reset) {

@@ -11,6 +11,8 @@
 
 #include <mutex>
 
+#include <cuda.h>
+
 #include "sfft4_internal.cuh"
 
 namespace sfft4 {
@@ -30,35 +32,69 @@ constexpr int64_t kNoallocMaxW = 131072;
 static __device__ __align__(256) double g_window_scratch[kNoallocMaxW];
 
 std::mutex g_setup_mu;
-double* g_scratch_ptr[64] = {nullptr};
+// Per device: the id of the context in which the scratch address was looked up, and the
+// address.  A device whose context was destroyed (cudaDeviceReset) and created again gets a
+// new context id, so the address is looked up again rather than reused.
+struct ScratchCache {
+    unsigned long long ctx_id = 0;
+    double* ptr = nullptr;
+};
+ScratchCache g_scratch[64];
 
-// Device address of the scratch array on the current device, looked up once per device.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+// Unique id of the calling thread's current CUDA context (0 if none is current yet), through
+// the driver entry points the runtime hands out (no link-time dependency on the driver).
+// Called with g_setup_mu held.
+int current_context_id(unsigned long long* id) {
+    *id = 0;
+    if (!g_ctx_get_current || !g_ctx_get_id) {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        int rc = sfft4::check_cuda(cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000,
+                                                                    cudaEnableDefault, &q1));
+        if (!rc) rc = sfft4::check_cuda(cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000,
+                                                                         cudaEnableDefault, &q2));
+        if (rc) return rc;
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return SFFT4_ECUDA;
+        g_ctx_get_current = (CtxGetCurrentFn)f1;
+        g_ctx_get_id = (CtxGetIdFn)f2;
+    }
+    CUcontext ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) return SFFT4_ECUDA;
+    if (!ctx) return SFFT4_OK;
+    return g_ctx_get_id(ctx, id) == CUDA_SUCCESS ? SFFT4_OK : SFFT4_ECUDA;
+}
+
+// Device address of the scratch array in the current device's current context, looked up
+// once per device and context (host code cannot use the symbol itself: it names a host-side
+// stand-in, not device memory).
 int scratch_address(double** out) {
     int dev = 0;
     int rc = sfft4::check_cuda(cudaGetDevice(&dev));
     if (rc) return rc;
     if (dev < 0 || dev >= 64) return SFFT4_ECUDA;
     std::lock_guard<std::mutex> lk(g_setup_mu);
-    if (!g_scratch_ptr[dev]) {
+    unsigned long long id = 0;
+    rc = current_context_id(&id);
+    if (rc) return rc;
+    ScratchCache& c = g_scratch[dev];
+    if (id == 0 || c.ctx_id != id || !c.ptr) {
         void* p = nullptr;
-        rc = sfft4::check_cuda(cudaGetSymbolAddress(&p, g_window_scratch));
+        rc = sfft4::check_cuda(cudaGetSymbolAddress(&p, g_window_scratch));  // makes the context current
         if (rc) return rc;
-        g_scratch_ptr[dev] = (double*)p;
+        rc = current_context_id(&id);
+        if (rc) return rc;
+        c.ctx_id = id;
+        c.ptr = (double*)p;
     }
-    *out = g_scratch_ptr[dev];
+    *out = c.ptr;
     return SFFT4_OK;
-}
-
-double erfcinv_newton(double y) {
-    double x = sqrt(-log(y));
-    for (int i = 0; i < 100; ++i) {
-        double f = erfc(x) - y;
-        double d = -2.0 / sqrt(M_PI) * exp(-x * x);
-        double step = f / d;
-        x -= step;
-        if (fabs(step) <= 1e-17 * fabs(x)) break;
-    }
-    return x;
 }
 
 }  // namespace
@@ -72,9 +108,8 @@ int sfft4_window_noalloc(int64_t N, int32_t B, double delta, float* G_dev, int64
     if (!(delta > 0 && delta < 0.5) || !G_dev || !Ghat_dev) return SFFT4_EINVAL;
     int n = 0;
     while ((int64_t(1) << n) < N) ++n;
-    const double c = 4.0 * sqrt(2.0) * erfcinv_newton(delta);
-    const double s_t = (double)B * c / (2.0 * M_PI);
-    const int64_t h = (int64_t)ceil(s_t * sqrt(2.0 * log(1.0 / delta)));
+    double s_t = 0.0;
+    const int64_t h = sfft4::window_halfwidth(B, delta, &s_t);
     const int64_t w = 2 * h + 1, L = N / B, nk = (3 * L) / 2 + 1;
     if (w > kNoallocMaxW || w > N / 2) return SFFT4_EINVAL;  // beyond the scratch maximum
     if (G_cap < w || Ghat_cap < nk) return SFFT4_EINVAL;

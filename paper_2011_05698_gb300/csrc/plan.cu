@@ -28,31 +28,6 @@ int ilog2(int64_t v) {
     return r;
 }
 
-// Inverse complementary error function by Newton's method on erfc (0 < y < 1).
-double erfcinv_newton(double y) {
-    // start from the asymptotic form erfc(x) ~ exp(-x^2) / (x sqrt(pi)) for small y
-    double x = (y < 0.5) ? sqrt(-log(y)) : 0.0;
-    if (y >= 0.5) x = (1.0 - y) * 0.886226925452758;  // erfinv(z) ~ sqrt(pi)/2 z
-    for (int i = 0; i < 100; ++i) {
-        double f = erfc(x) - y;
-        double d = -2.0 / sqrt(M_PI) * exp(-x * x);
-        double step = f / d;
-        x -= step;
-        if (fabs(step) <= 1e-17 * fabs(x)) break;
-    }
-    return x;
-}
-
-// Window half-width: frequency box of half-width 3L/4 convolved with a Gaussian of std
-// s_f = L / (4 sqrt 2 erfcinv(delta)); in time a Gaussian of std s_t = N / (2 pi s_f),
-// truncated at delta: h = ceil(s_t sqrt(2 ln(1/delta))) (flat window of Eq. 9).
-int64_t window_halfwidth(int64_t B, double delta, double* s_t_out) {
-    double c = 4.0 * sqrt(2.0) * erfcinv_newton(delta);
-    double s_t = (double)B * c / (2.0 * M_PI);
-    if (s_t_out) *s_t_out = s_t;
-    return (int64_t)ceil(s_t * sqrt(2.0 * log(1.0 / delta)));
-}
-
 // Nominal level lengths of a region of length L0 (Section 3.2): Lbar_{s+1} =
 // ceil((q+1) Lbar_s / l) + 1 while Lbar_s > l and the length still shrinks.
 std::vector<int64_t> levels(int64_t L0, int l, int qn) {
@@ -139,6 +114,7 @@ void free_plan(sfft4_plan_s* p) {
         if (p->ev_done[s]) cudaEventDestroy(p->ev_done[s]);
         if (p->astream[s]) cudaStreamDestroy(p->astream[s]);
     }
+    if (p->ev_sync) cudaEventDestroy(p->ev_sync);
     for (sfft4_plan_s* q : p->peer) free_plan(q);
     sfft4::destroy_group(p->grp);
     delete p;
@@ -147,6 +123,32 @@ void free_plan(sfft4_plan_s* p) {
 }  // namespace
 
 namespace sfft4 {
+
+// Inverse complementary error function by Newton's method on erfc (0 < y < 1).
+double erfcinv_newton(double y) {
+    // start from the asymptotic form erfc(x) ~ exp(-x^2) / (x sqrt(pi)) for small y
+    double x = (y < 0.5) ? sqrt(-log(y)) : 0.0;
+    if (y >= 0.5) x = (1.0 - y) * 0.886226925452758;  // erfinv(z) ~ sqrt(pi)/2 z
+    for (int i = 0; i < 100; ++i) {
+        double f = erfc(x) - y;
+        double d = -2.0 / sqrt(M_PI) * exp(-x * x);
+        double step = f / d;
+        x -= step;
+        if (fabs(step) <= 1e-17 * fabs(x)) break;
+    }
+    return x;
+}
+
+// Window half-width: frequency box of half-width 3L/4 convolved with a Gaussian of std
+// s_f = L / (4 sqrt 2 erfcinv(delta)); in time a Gaussian of std s_t = N / (2 pi s_f),
+// truncated at delta: h = ceil(s_t sqrt(2 ln(1/delta))) (flat window of Eq. 9).
+int64_t window_halfwidth(int64_t B, double delta, double* s_t_out) {
+    double c = 4.0 * sqrt(2.0) * erfcinv_newton(delta);
+    double s_t = (double)B * c / (2.0 * M_PI);
+    if (s_t_out) *s_t_out = s_t;
+    return (int64_t)ceil(s_t * sqrt(2.0 * log(1.0 / delta)));
+}
+
 int check_cuda(cudaError_t e) {
     if (e == cudaSuccess) return SFFT4_OK;
     snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
@@ -424,6 +426,9 @@ int sfft4_plan(sfft4_plan_t* out, int64_t N, int64_t K, int32_t l, double q, uin
     int qn = 0;
     int rc0 = plan_options(N, K, l, q, opts, &o, &qn);
     if (rc0) return rc0;
+    // the iteration-major fold puts the signals of a batch in grid.y (at most 65535)
+    if (o.fold_order == SFFT4_FOLD_ITERATION_MAJOR && o.max_batch > 65535) return SFFT4_EINVAL;
+    if (o.trace && (o.trace_signal < 0 || o.trace_signal >= o.max_batch)) return SFFT4_EINVAL;
     sfft4_plan_s* p = new (std::nothrow) sfft4_plan_s();
     if (!p) return SFFT4_ENOMEM;
     p->N = N;

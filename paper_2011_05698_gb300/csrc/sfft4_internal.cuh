@@ -249,6 +249,10 @@ struct sfft4_plan_s {
     cudaEvent_t ev_in[sfft4::kAsyncDepth] = {};
     cudaEvent_t ev_done[sfft4::kAsyncDepth] = {};
     int async_next = 0, async_used = 0;
+    // end of the latest synchronous execute (or bucketization) on the plan's own workspace, on
+    // the caller's stream; an asynchronous execute that takes slot 0 waits for it
+    cudaEvent_t ev_sync = nullptr;
+    bool sync_pending = false;
     int32_t* status = nullptr;  // 1 when a bounded device wait gave up
     int sm_count = 0;
     float* theta = nullptr;     // [sig] candidate floor
@@ -303,8 +307,10 @@ int build_signal_major_fold(sfft4_plan_s* p);
 // after the execute reads its inputs behind the work queued on `caller`; async_end marks it.
 int async_begin(sfft4_plan_s* p, cudaStream_t caller, sfft4_plan_s** w, cudaStream_t* as);
 int async_end(sfft4_plan_s* p, cudaStream_t as);
-// A synchronous execute waits for the asynchronous one that used the plan's own workspace.
+// A synchronous execute waits for the asynchronous one that used the plan's own workspace;
+// mark_sync records its end, which the next asynchronous execute in slot 0 waits for.
 int join_slot0(sfft4_plan_s* p, cudaStream_t st);
+int mark_sync(sfft4_plan_s* p, cudaStream_t st);
 int launch_fold_signal_major(sfft4_plan_s* p, int nsig, const float2* x, int64_t x_stride, cudaStream_t st);
 int launch_fold_multi(int RG, const FoldArgs* jobs, const FoldTile* tiles, int ntiles,
                       const float2* const* xptrs, int threads, size_t smem, cudaStream_t st);
@@ -330,6 +336,11 @@ void destroy_group(Group* g);
 size_t group_levels(const Group* g);
 const FinalJob* group_final_jobs(const Group* g, int* nsig, int64_t* samples, int* kernels);
 // Implemented in plan.cu.
+// Half-width h of the flat window of B buckets at leakage delta (Eq. 9, the window design of
+// a Gaussian of time-domain std s_t = B 4 sqrt2 erfcinv(delta) / (2 pi) truncated at delta):
+// h = ceil(s_t sqrt(2 ln(1/delta))); *s_t_out (if not NULL) receives s_t.  The one definition
+// every table builder uses.
+int64_t window_halfwidth(int64_t B, double delta, double* s_t_out);
 int plan_options(int64_t N, int64_t K, int32_t l, double q, const sfft4_opts* opts, sfft4_opts* out,
                  int* qn_out);
 int plan_schedule(sfft4_plan_s* p);

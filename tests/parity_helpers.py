@@ -25,11 +25,12 @@ def found_set_from(f, v, vt):
     return fs
 
 
-def explain_divergence(p, r, N, K, l, q, seed, B1=0):
-    """Walk the iterations of the GPU trace (plan made with trace=True, signal 0) and the
-    oracle trace; at the first iteration whose found sets differ, the oracle must have had a
-    fragile decision and its decode fed the GPU's own buckets must reproduce the GPU's found
-    set.  Returns that iteration (or None when the traces never part)."""
+def explain_divergence(p, r, N, K, l, q, seed, B1=0, signal=0):
+    """Walk the iterations of the GPU trace (plan made with trace=True, tracing batch index
+    `signal`) and the oracle trace of that signal (run with signal=`signal`); at the first
+    iteration whose found sets differ, the oracle must have had a fragile decision and its
+    decode fed the GPU's own buckets must reproduce the GPU's found set.  Returns that
+    iteration (or None when the traces never part)."""
     op = OP.make_plan(N, K, l, q, seed=seed, B1=B1)
     wc = OW.WindowCache(N, op.delta)
     prev = O.FoundSet()
@@ -41,9 +42,34 @@ def explain_divergence(p, r, N, K, l, q, seed, B1=0):
             continue
         assert fragile(tr), ("divergence without a fragile margin", tr["m"])
         it = op.iters[tr["m"] - 1]
-        sigma, a = philox.permutation_draw(seed, 0, it.m, N)
+        sigma, a = philox.permutation_draw(seed, signal, it.m, N)
         _, _, Ghat = wc.get(it.B)
         out, _ = O.decode_iteration(Y.astype(np.complex128), prev, it, op, sigma, a, r["theta"], Ghat)
         assert list(out.f) == [int(x) for x in f], ("replay does not reproduce the GPU", tr["m"])
         return tr["m"]
     return None
+
+
+def assert_oracle_parity(f, v, vt, r, explain, value_tol):
+    """The bar of a GPU result (f, v, vt: support, values, votes) against the oracle's run of
+    the same signal, r (run with trace=True):
+
+    * support and votes equal to the oracle's, values within `value_tol` relative l2; or
+    * the runs part, and `explain()` (a traced GPU run of the same signal through
+      explain_divergence) shows that they part first at a fragile oracle decision that the
+      oracle's own decode, replayed on the GPU's bucket arrays, reproduces.  From that
+      iteration on the two runs continue from different found sets, so what follows is only
+      checked for sanity: nearly the same support, values close on the common part.
+
+    Returns the iteration of an explained divergence, or None."""
+    if np.array_equal(f, r["f"]) and np.array_equal(vt, r["votes"]):
+        rel = np.linalg.norm(v - r["v"]) / max(np.linalg.norm(r["v"]), 1e-300)
+        assert rel <= value_tol, rel
+        return None
+    m = explain()
+    assert m is not None, "the final results differ but the traces never part"
+    common = np.intersect1d(f, r["f"])
+    assert common.size >= 0.95 * max(len(f), len(r["f"]))
+    gi, oi = np.searchsorted(f, common), np.searchsorted(r["f"], common)
+    assert np.linalg.norm(v[gi] - r["v"][oi]) <= 1e-2 * np.linalg.norm(r["v"][oi])
+    return m

@@ -68,20 +68,18 @@ def test_round_count_extremes_match_oracle(s4, l, q, precision):
 
 
 def test_round_count_extremes_noisy(s4):
-    """l = 4, q = 1 at 20 dB: support overlap >= 98 % and values within 1e-4 on the common
-    support (decisions may part at fragile margins under noise)."""
-    N, K, l, q, seed = 2**20, 100, 4, 1.0, 5
-    sig = sparse_signal(N, K, seed, 20.0)
-    p = s4.Plan(N, K, l, q, seed=seed)
-    idx, val, nf, _ = p.execute(to_dev(sig.x))
-    n = int(nf.item())
-    f, v = idx[:n].cpu().numpy(), val[:n].cpu().numpy()
-    r = O.run(sig.x.astype(np.complex128), OP.make_plan(N, K, l, q, seed=seed))
-    common = np.intersect1d(f, r["f"])
-    assert common.size >= 0.98 * max(n, len(r["f"]))
-    gi, oi = np.searchsorted(f, common), np.searchsorted(r["f"], common)
-    assert np.linalg.norm(v[gi] - r["v"][oi]) <= 1e-4 * np.linalg.norm(r["v"][oi])
-    p.close()
+    """l = 4, q = 1 at 20 dB: support and votes equal to the oracle's, values within 1e-4,
+    unless the runs part at a fragile decision explained by replay."""
+    N, K, l, q = 2**20, 100, 4, 1.0
+    for seed in (5, 6):
+        sig = sparse_signal(N, K, seed, 20.0)
+        p = s4.Plan(N, K, l, q, seed=seed, trace=True)
+        idx, val, nf, votes = p.execute(to_dev(sig.x))
+        n = int(nf.item())
+        f, v, vt = idx[:n].cpu().numpy(), val[:n].cpu().numpy(), votes[:n].cpu().numpy()
+        r = O.run(sig.x.astype(np.complex128), OP.make_plan(N, K, l, q, seed=seed), trace=True)
+        PH.assert_oracle_parity(f, v, vt, r, lambda: PH.explain_divergence(p, r, N, K, l, q, seed), 1e-4)
+        p.close()
 
 
 def bucket_check(s4, N, K, l, q, seed, snr, ms, precision):

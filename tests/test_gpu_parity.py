@@ -177,17 +177,18 @@ def test_end_to_end_noiseless(s4, name, seeds, precision):
         p.close()
 
 
-def test_end_to_end_noisy_support_and_values(s4):
-    """At 20 dB the decisions of the FP32 path and the FP64 oracle can part at fragile
-    margins; on these seeds they do not, and values agree to 1e-4."""
-    sig, (f, v, vt, _, _), r, p = e2e(s4, "c2", 0, snr=20.0)
-    p.close()
-    common = np.intersect1d(f, r["f"])
-    assert common.size >= 0.98 * max(len(f), len(r["f"]))
-    gi = np.searchsorted(f, common)
-    oi = np.searchsorted(r["f"], common)
-    rel = np.linalg.norm(v[gi] - r["v"][oi]) / np.linalg.norm(r["v"][oi])
-    assert rel <= 1e-4
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("name,seeds", [("c1", range(3)), ("c2", range(3))])
+def test_end_to_end_noisy_exact(s4, name, seeds, precision):
+    """At 20 dB: support and votes equal to the oracle's and values within 1e-4 relative l2,
+    unless the runs part at a fragile decision that the replay of the GPU's own bucket arrays
+    explains (the FP32 buckets and the FP64 oracle may legitimately decide a near-tie
+    differently)."""
+    N, K, l, q, B1 = WORKLOADS[name]
+    for seed in seeds:
+        sig, (f, v, vt, _, _), r, p = e2e(s4, name, seed, snr=20.0, trace=True, precision=precision)
+        PH.assert_oracle_parity(f, v, vt, r, lambda: explain_divergence(p, r, name, seed), 1e-4)
+        p.close()
 
 
 @pytest.mark.parametrize("name,seed,snr", [("c2", 0, 20.0), ("c2", 1, None), ("c1", 2, 20.0)])

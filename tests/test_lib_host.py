@@ -48,13 +48,13 @@ def test_struct_layouts_match_c(tmp_path):
     from paper_2011_05698_gb300 import _lib
     src = tmp_path / "sz.c"
     src.write_text('#include "sfft4.h"\n#include <stdio.h>\n#include <stddef.h>\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(sfft4_opts), '
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(sfft4_opts), '
                    'sizeof(sfft4_plan_info), sizeof(sfft4_iter_info), offsetof(sfft4_iter_info, tau), '
                    'offsetof(sfft4_iter_info, unique_samples), sizeof(sfft4_c128), '
                    'offsetof(sfft4_opts, graph), sizeof(sfft4_batch_info), '
                    'offsetof(sfft4_batch_info, samples_per_execute), sizeof(sfft4_run_stats), '
                    'offsetof(sfft4_run_stats, votes_hist), offsetof(sfft4_opts, location), '
-                   'offsetof(sfft4_opts, fold_order)); return 0;}\n')
+                   'offsetof(sfft4_opts, fold_order), offsetof(sfft4_opts, trace_signal)); return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
@@ -62,7 +62,7 @@ def test_struct_layouts_match_c(tmp_path):
             _lib.IterInfo.tau.offset, _lib.IterInfo.unique_samples.offset, ctypes.sizeof(_lib.C128),
             _lib.Opts.graph.offset, ctypes.sizeof(_lib.BatchInfo), _lib.BatchInfo.samples_per_execute.offset,
             ctypes.sizeof(_lib.RunStats), _lib.RunStats.votes_hist.offset, _lib.Opts.location.offset,
-            _lib.Opts.fold_order.offset]
+            _lib.Opts.fold_order.offset, _lib.Opts.trace_signal.offset]
     assert got == want
 
 
@@ -110,6 +110,21 @@ def test_plan_rejects_bad_options(lib):
         h = ctypes.c_void_p()
         assert lib.sfft4_plan(ctypes.byref(h), 2**14, 16, 4, 0.5, 0, ctypes.byref(o)) == _lib.SFFT4_EINVAL
     assert lib.sfft4_plan(None, 2**14, 16, 4, 0.5, 0, None) == _lib.SFFT4_EINVAL
+    # the iteration-major fold puts the batch in grid.y: more than 65535 signals is rejected at
+    # plan time (before any device work), not at the first launch
+    o = _lib.Opts()
+    lib.sfft4_opts_default(ctypes.byref(o))
+    o.fold_order = _lib.SFFT4_FOLD_ITERATION_MAJOR
+    o.max_batch = 65536
+    h = ctypes.c_void_p()
+    assert lib.sfft4_plan(ctypes.byref(h), 2**14, 16, 4, 0.5, 0, ctypes.byref(o)) == _lib.SFFT4_EINVAL
+    assert not h.value
+    # the traced signal must be a signal of the batch
+    for ts in (-1, 4):
+        o = _lib.Opts()
+        lib.sfft4_opts_default(ctypes.byref(o))
+        o.trace, o.max_batch, o.trace_signal = 1, 4, ts
+        assert lib.sfft4_plan(ctypes.byref(h), 2**14, 16, 4, 0.5, 0, ctypes.byref(o)) == _lib.SFFT4_EINVAL
 
 
 def test_execute_rejects_null_arguments(lib):
@@ -124,6 +139,8 @@ def test_execute_rejects_null_arguments(lib):
     assert lib.sfft4_execute_batched_async(None, 1, None, 0, None, None, None, None, None) == _lib.SFFT4_EINVAL
     assert lib.sfft4_wait(None, None) == _lib.SFFT4_EINVAL
     assert lib.sfft4_execute_batched_v_async(None, None, None, None, None, None, None) == _lib.SFFT4_EINVAL
+    assert lib.sfft4_sync_status(None) == _lib.SFFT4_EINVAL
+    assert lib.sfft4_inject_status(None, 1) == _lib.SFFT4_EINVAL
     lib.sfft4_destroy(None)
 
 
