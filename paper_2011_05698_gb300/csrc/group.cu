@@ -225,6 +225,7 @@ int build_group_plan(sfft4_plan_s* p, int nsig, const int64_t* Ns, const int64_t
                 }
             }
             f.n = (int)((int64_t)tiles.size() - f.off);
+            f.smem = fold_smem(f.RG, f.threads);
             if (f.n > 0) L.folds.push_back(f);
         }
         // DFT columns by bucket count

@@ -175,56 +175,33 @@ constexpr int kFoldUnroll = 4;
 // t = rho + m' B with rho = slice Wj + jj and m' = p (mod P), so its fold slot for round s,
 // (t - tau_s) mod B, is fixed: it accumulates in registers, then the P copies of each slot
 // are summed in a fixed order.  Each x sample is loaded once for all rounds whose window
-// covers it.  The window coefficients the CTA needs, G[rho + m' B - tau_s + h], are staged
-// in shared memory at the start (rows m' of Wj contiguous coefficients, zero outside the
-// window), so the main loop issues only the random gathers of x.  Index arithmetic is exact
-// in 32 bits: N = 2^n divides 2^32, so (sigma t + a) mod N is the low n bits of the wrapped
-// 32-bit value.
+// covers it; its window coefficient for round s, G[t - tau_s + h], is loaded from the table
+// beside it (the 32 lanes of a warp hold consecutive residues, so the coefficient loads of a
+// warp are contiguous).  The copies of every round are summed after one barrier.  Index
+// arithmetic is exact in 32 bits: N = 2^n divides 2^32, so (sigma t + a) mod N is the low n
+// bits of the wrapped 32-bit value.  red: shared memory of RG x blockDim.x float2.
 template <int RG>
 __device__ __forceinline__ void fold_body(const FoldArgs& a, int slice, int64_t signal_index,
-                                          const float2* __restrict__ x, float2* zsig, float* gsm,
-                                          uint32_t* s_par, float2* red) {
-    const int tid = threadIdx.x;
-    const int Wj = a.Wj, B = a.B, Mrows = a.Mrows;
+                                          const float2* __restrict__ x, float2* zsig, float2* red) {
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int Wj = a.Wj, B = a.B;
     const int P = a.g.P;
     const bool active = tid < Wj * P;  // a launch may carry more threads than this job uses
     const int jj = tid % Wj, p = tid / Wj;
     const int rho0 = slice * Wj;
-    if (tid == 0) {
+    uint32_t sigma, aoff;
+    {
+        // the same draw in every thread (block-uniform, no barrier needed)
         uint64_t s, o;
         permutation_draw(a.seed, (uint64_t)signal_index, (uint64_t)a.m, a.N, &s, &o);
-        s_par[0] = (uint32_t)s;
-        s_par[1] = (uint32_t)o;
+        sigma = (uint32_t)s;
+        aoff = (uint32_t)o;
     }
-    // stage the window rows of this residue slice: thread (jj, p) fills column jj of rows
-    // p, p + P, ... of every round, four loads in flight (rows of a warp are coalesced)
-    const float* __restrict__ G = a.G;
-    if (active) {
-        for (int s = 0; s < a.g.nr; ++s) {
-            const int g0 = rho0 + jj + a.mlo[s] * B - a.tau[s] + a.h;  // G index of row 0
-            float* dst = gsm + (s * Mrows) * Wj + jj;
-            int row = p;
-            for (; row + 3 * P < Mrows; row += 4 * P) {
-                float gv[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int gi = g0 + (row + u * P) * B;
-                    gv[u] = (gi >= 0 && gi < a.w) ? __ldg(G + gi) : 0.f;
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) dst[(row + u * P) * Wj] = gv[u];
-            }
-            for (; row < Mrows; row += P) {
-                const int gi = g0 + row * B;
-                dst[row * Wj] = (gi >= 0 && gi < a.w) ? __ldg(G + gi) : 0.f;
-            }
-        }
-    }
-    __syncthreads();
-    const uint32_t sigma = s_par[0], aoff = s_par[1], mask = (uint32_t)(a.N - 1);
+    const uint32_t mask = (uint32_t)(a.N - 1);
     const int PB = P * B;
     const int rho = rho0 + jj + p * B;  // residue mod P B
     const uint32_t step = sigma * (uint32_t)PB;
+    const float* __restrict__ G = a.G;
     float2 acc[RG];
 #pragma unroll
     for (int s = 0; s < RG; ++s) acc[s] = make_float2(0.f, 0.f);
@@ -238,10 +215,7 @@ __device__ __forceinline__ void fold_body(const FoldArgs& a, int slice, int64_t 
         if (t >= t1) continue;
         const int cnt = (t1 - t + PB - 1) / PB;
         uint32_t idx = sigma * (uint32_t)t + aoff;
-        // shared-memory row of sample k of round s: (t + k P B - rho0 - jj) / B - mlo_s
-        const int m0 = (t - rho0 - jj) >> a.logB;
-        const int rowbase = m0 * Wj + jj;
-        const int rowstep = P * Wj;
+        const int gi0 = t + a.h;  // G index of sample k of round s: gi0 + k P B - tau_s
         for (int k = 0; k < cnt; k += kFoldUnroll) {
             float2 v[kFoldUnroll];
 #pragma unroll
@@ -255,7 +229,7 @@ __device__ __forceinline__ void fold_body(const FoldArgs& a, int slice, int64_t 
 #pragma unroll
                     for (int s = 0; s < RG; ++s) {
                         if ((rm >> s) & 1u) {
-                            const float gw = gsm[a.soff[s] + rowbase + (k + u) * rowstep];
+                            const float gw = __ldg(G + (gi0 + (k + u) * PB - a.tau[s]));
                             acc[s].x = fmaf(gw, v[u].x, acc[s].x);
                             acc[s].y = fmaf(gw, v[u].y, acc[s].y);
                         }
@@ -264,35 +238,32 @@ __device__ __forceinline__ void fold_body(const FoldArgs& a, int slice, int64_t 
             }
         }
     }
+    // the P copies of each (round, slot), summed in copy order 0 .. P-1
 #pragma unroll
-    for (int s = 0; s < RG; ++s) {
-        if (s < a.g.nr) {
-            red[tid] = acc[s];
-            __syncthreads();
-            if (p == 0 && active) {
-                float2 sum = red[jj];
-                for (int pp = 1; pp < P; ++pp) {
-                    float2 o = red[jj + pp * Wj];
-                    sum.x += o.x;
-                    sum.y += o.y;
-                }
-                int slot = (rho0 + jj - a.tau[s]) % B;
-                if (slot < 0) slot += B;
-                if (active) zsig[(int64_t)(a.g.r0 + s) * B + slot] = sum;
-            }
-            __syncthreads();
+    for (int s = 0; s < RG; ++s)
+        if (s < a.g.nr) red[s * T + tid] = acc[s];
+    __syncthreads();
+    for (int e = tid; e < a.g.nr * Wj; e += T) {
+        const int s = e / Wj, j = e - s * Wj;
+        const float2* rs = red + s * T + j;
+        float2 sum = rs[0];
+        for (int pp = 1; pp < P; ++pp) {
+            const float2 o = rs[pp * Wj];
+            sum.x += o.x;
+            sum.y += o.y;
         }
+        int slot = (rho0 + j - a.tau[s]) % B;
+        if (slot < 0) slot += B;
+        zsig[(int64_t)(a.g.r0 + s) * B + slot] = sum;
     }
 }
 
 template <int RG>
 __global__ void __launch_bounds__(512, 2) k_fold(const FoldArgs a) {
-    extern __shared__ float gsm[];  // [RG][Mrows][Wj]
-    __shared__ uint32_t s_par[2];
-    __shared__ float2 red[512];
+    extern __shared__ float2 red[];  // [RG][blockDim.x]
     const int sig = blockIdx.y;
     fold_body<RG>(a, blockIdx.x, (int64_t)a.signal0 + sig, a.x + (int64_t)sig * a.x_stride,
-                  a.z + (int64_t)sig * a.z_stride, gsm, s_par, red);
+                  a.z + (int64_t)sig * a.z_stride, red);
 }
 
 // Tile queue of a batch of signals with different N and K: CTA b takes tile tiles[b] = (job,
@@ -303,15 +274,13 @@ template <int RG>
 __global__ void __launch_bounds__(512, 2) k_fold_multi(const FoldArgs* __restrict__ jobs,
                                                        const FoldTile* __restrict__ tiles,
                                                        const float2* const* __restrict__ xptrs) {
-    extern __shared__ float gsm[];
-    __shared__ uint32_t s_par[2];
-    __shared__ float2 red[512];
+    extern __shared__ float2 red[];  // [RG][blockDim.x]
     __shared__ __align__(16) FoldArgs sa;
     const FoldTile t = tiles[blockIdx.x];
     for (int i = threadIdx.x; i < (int)(sizeof(FoldArgs) / 4); i += blockDim.x)
         ((uint32_t*)&sa)[i] = ((const uint32_t*)(jobs + t.job))[i];
     __syncthreads();
-    fold_body<RG>(sa, t.slice, sa.signal0, xptrs[sa.signal0], sa.z, gsm, s_par, red);
+    fold_body<RG>(sa, t.slice, sa.signal0, xptrs[sa.signal0], sa.z, red);
 }
 
 // Signal-major fold of a uniform batch: CTA b folds tile b mod ntiles of signal b / ntiles,
@@ -322,16 +291,14 @@ __global__ void __launch_bounds__(512, 2) k_fold_multi(const FoldArgs* __restric
 // parameter space (indexed by a block-uniform job number).
 template <int RG>
 __global__ void __launch_bounds__(512, 2) k_fold_sig(const __grid_constant__ SigFoldLaunch L) {
-    extern __shared__ float gsm[];
-    __shared__ uint32_t s_par[2];
-    __shared__ float2 red[512];
+    extern __shared__ float2 red[];  // [RG][blockDim.x]
     const int sig = blockIdx.x / L.ntiles;
     const int ti = blockIdx.x - sig * L.ntiles;
     int j = 0;
     while (j + 1 < L.njobs && ti >= L.start[j + 1]) ++j;
     const FoldArgs& a = L.jobs[j];
     fold_body<RG>(a, ti - L.start[j], (int64_t)a.signal0 + sig, L.x + (int64_t)sig * L.x_stride,
-                  a.z + (int64_t)sig * a.z_stride, gsm, s_par, red);
+                  a.z + (int64_t)sig * a.z_stride, red);
 }
 
 // ----------------------------------------------------------------- FFT --------------
@@ -1264,18 +1231,8 @@ FoldArgs make_fold_args(const sfft4_plan_s* p, int mi, const FoldGroup& g, size_
     a.w = 2 * d.h + 1;
     a.G = d.G;
     a.g = g;
-    // rows m' of B with tau_s - h <= rho + m' B <= tau_s + h for some rho in [0, B)
-    int Mrows = 0;
-    for (int s = 0; s < kFoldRG; ++s) {
-        a.tau[s] = (s < g.nr) ? (int32_t)d.tau[g.r0 + s] : 0;
-        int64_t lo = floor_div(a.tau[s] - (int64_t)d.h - (d.B - 1), d.B);
-        int64_t hi = floor_div(a.tau[s] + (int64_t)d.h, d.B);
-        a.mlo[s] = (int32_t)lo;
-        if (s < g.nr) Mrows = std::max<int>(Mrows, (int)(hi - lo + 1));
-    }
-    a.Mrows = Mrows;
-    for (int s = 0; s < kFoldRG; ++s) a.soff[s] = (s * Mrows - a.mlo[s]) * ih.Wj;
-    if (smem_out) *smem_out = (size_t)g.nr * Mrows * ih.Wj * sizeof(float);
+    for (int s = 0; s < kFoldRG; ++s) a.tau[s] = (s < g.nr) ? (int32_t)d.tau[g.r0 + s] : 0;
+    if (smem_out) *smem_out = fold_smem(g.nr, ih.Wj * g.P);
     return a;
 }
 
@@ -1454,6 +1411,7 @@ int build_signal_major_fold(sfft4_plan_s* p) {
         }
         h.L.njobs = (int32_t)(j1 - j0);
         h.L.ntiles = h.L.start[h.L.njobs];
+        h.smem = fold_smem(h.RG, h.threads);
         if ((int64_t)h.L.ntiles * p->o.max_batch > (int64_t)INT32_MAX || h.threads > 512 ||
             h.smem > (size_t)kFoldSmemMax)
             return SFFT4_EINVAL;

@@ -310,15 +310,9 @@ int plan_schedule(sfft4_plan_s* p) {
         }
         // fold groups of up to kFoldRG rounds
         // residues per fold CTA: 32 (measured against 16 and 64: small enough that the
-        // CTAs resident at a time cover few signals in signal-major order, wide enough for
-        // coalesced window-row staging), fewer when the staged window rows of a CTA
-        // (rounds x rows x residues floats) would exceed the shared-memory budget
+        // CTAs resident at a time cover few signals in signal-major order; one warp's window
+        // coefficient loads are then 32 contiguous floats)
         ih.Wj = (int32_t)std::min<int64_t>(B, 32);
-        {
-            int64_t rows = (2 * (int64_t)d.h + B) / B + 2;
-            while (ih.Wj > 16 && (int64_t)kFoldRG * rows * ih.Wj * 4 > kFoldSmemMax) ih.Wj >>= 1;
-            if ((int64_t)kFoldRG * rows * ih.Wj * 4 > kFoldSmemMax) return SFFT4_EINVAL;
-        }
         ih.unique = 0;
         // balanced groups of at most kFoldGroupMax rounds (the fold kernel's accumulator count
         // is the largest group of its launch)

@@ -28,7 +28,7 @@ constexpr int kAsyncDepth = 3;          // most workspaces of the asynchronous e
 // for a batch of uneven signals (folded level by level; its step is its decode chain, and
 // two chains overlap: 78 K against 66 K transforms/s on the 512-signal workload).
 inline int async_depth(bool uneven) { return uneven ? 3 : 2; }
-constexpr int kFoldSmemMax = 100 * 1024;     // staged window rows of one fold CTA
+constexpr int kFoldSmemMax = 32 * 1024;      // per-copy sums of one fold CTA (8 rounds x 512 threads)
 
 // Rounds [r0, r0 + nr) of one iteration that one fold launch accumulates, and the
 // t-segments covering the union of their windows [tau_s - h, tau_s + h]; within a segment
@@ -85,13 +85,15 @@ struct FoldArgs {
     float2* z;
     int64_t z_stride;
     uint64_t N, seed;
-    int32_t m, signal0, B, logB, Wj, h, w, Mrows;
+    int32_t m, signal0, B, logB, Wj, h, w;
     const float* G;
     FoldGroup g;
     int32_t tau[kFoldRG];
-    int32_t mlo[kFoldRG];   // first multiple m' of B with rows of round s in shared memory
-    int32_t soff[kFoldRG];  // (s Mrows - mlo_s) Wj: shared-memory offset of round s
 };
+
+// Dynamic shared memory of a fold launch of `threads` threads whose jobs have at most rg
+// rounds: the per-copy sums of every round (rg x threads float2).
+inline size_t fold_smem(int rg, int threads) { return (size_t)rg * threads * 8; }
 
 struct FoldTile {
     int32_t job, slice;
