@@ -213,6 +213,47 @@ def fold_traffic_record():
         return None
 
 
+def gather_sweep(s4, xs, sm_count, footprints, inflights=(4, 8, 16), fetches=(32, 64, 128),
+                 shapes=((256, 2), (256, 4), (256, 8), (512, 1), (512, 2), (512, 4), (1024, 1), (1024, 2)),
+                 loads=150_000_000):
+    """Random 8-byte loads per second of sfft4_gather_probe_ex over a grid: footprint (rows of
+    xs read side by side, nsig x N x 8 bytes), loads in flight per thread, L2 fetch granularity,
+    (threads per CTA, CTAs per SM).  Returns the list of points, each with its rate."""
+    pts = []
+    for nsig in footprints:
+        x = xs[:nsig]
+        for inf in inflights:
+            for fb in fetches:
+                for th, cps in shapes:
+                    blocks = sm_count * cps
+                    iters = max(1, loads // (blocks * th * inf))
+                    lps = s4.gather_probe(x, blocks=blocks, iters=iters, threads=th, inflight=inf, l2_fetch_bytes=fb)
+                    pts.append({"nsig": nsig, "footprint_mb": nsig * x.shape[1] * 8 / 2**20, "inflight": inf,
+                                "l2_fetch_bytes": fb, "threads": th, "ctas_per_sm": cps, "gloads_s": lps / 1e9})
+    return pts
+
+
+def gather_ceiling_form(s4, dev):
+    """Sweep of the random-gather probe: footprints from one L2-resident 32 MB signal to 64
+    signals (2 GB), 4/8/16 loads in flight per thread, 32/64/128-byte L2 fetches, 256-1024
+    threads per CTA and 1-8 CTAs per SM.  Reports every point and the best per footprint."""
+    import torch
+    from synth.signals import device_signal
+    N, S = N_DEF, 64
+    xs = torch.empty((S, N), dtype=torch.complex64, device=dev)
+    for i in range(S):
+        device_signal(N, K_DEF, 5000 + i, None, dev, out=xs[i])
+    sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    pts = gather_sweep(s4, xs, sm, (1, 2, 4, 16, 64))
+    best = {}
+    for pt in pts:
+        b = best.get(pt["nsig"])
+        if b is None or pt["gloads_s"] > b["gloads_s"]:
+            best[pt["nsig"]] = pt
+    return {"form": "gather_ceiling", "N": N, "sm_count": sm, "points": pts,
+            "best_per_footprint": [best[k] for k in sorted(best)]}
+
+
 def device_batch(N, K, S, seed0, snr, device):
     """Seeded synthetic batch synthesised on the device (spectra drawn by synth)."""
     import torch
@@ -544,7 +585,8 @@ def main():
                     help="fold order of the headline plan")
     ap.add_argument("--no-async", action="store_true",
                     help="headline steps as synchronous executes (no overlap between batches)")
-    ap.add_argument("--form", default="all", choices=["all", "uneven", "sweep", "configs", "phase_error"],
+    ap.add_argument("--form", default="all", choices=["all", "uneven", "sweep", "configs", "phase_error",
+                                                      "gather_ceiling"],
                     help="uneven: time only the uneven-batch form; sweep: the large-N SNR x (l, q) "
                          "sweep (N = 2^26, K = 4000, 10 seeds)")
     ap.add_argument("--sweep-seeds", type=int, default=10)
@@ -576,6 +618,13 @@ def main():
     if args.form == "phase_error":
         if rank == 0:
             print(json.dumps(phase_error_form(s4, args, dev)), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    if args.form == "gather_ceiling":
+        if rank == 0:
+            print(json.dumps(gather_ceiling_form(s4, dev)), flush=True)
         if dist is not None:
             dist.destroy_process_group()
         return
@@ -653,8 +702,12 @@ def main():
     if tr is not None:
         traffic = tr["dram_bytes_per_sample"] * prof["fold_samples"] / launches
     # achievable rate of the gather's access pattern (random 8-byte loads inside each signal
-    # of this same batch), measured on this device
-    gather_lps = s4.gather_probe(xs)
+    # of this same batch, footprint far above L2), measured on this device: the best point of
+    # a sweep of loads in flight, L2 fetch granularity and CTA shape
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    sweep = gather_sweep(s4, xs, sm_count, (S,))
+    best_pt = max(sweep, key=lambda q: q["gloads_s"])
+    gather_lps = best_pt["gloads_s"] * 1e9
     gather_ceiling = 32.0 * gather_lps / 1e9  # GB/s of 32-byte sectors
     sector_gbs = 4.0 * achieved
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -663,6 +716,8 @@ def main():
                 "per_unit": "8 B per distinct sample read (complex64)",
                 "sector_frac": 4.0 * achieved / peak, "peak_kind": peak_kind,
                 "random_gather_ceiling_gbs": gather_ceiling,
+                "random_gather_ceiling_point": best_pt,
+                "fold_gsamples_s": prof["fold_samples"] / fold_s / 1e9 if fold_s > 0 else None,
                 "frac_of_random_gather_ceiling": sector_gbs / gather_ceiling if gather_ceiling > 0 else None,
                 "fold_share_of_step": prof["fold_ms"] / (1e3 * el) if el > 0 else None,
                 "kernel_ms": {k: prof[k + "_ms"] for k in ("fold", "fft", "decode", "finalize")}}

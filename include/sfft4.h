@@ -110,6 +110,12 @@ typedef struct {
                                 bucket arrays and found sets sfft4_trace_get returns (0 <=
                                 trace_signal < max_batch; an execute of fewer signals than
                                 trace_signal + 1 returns SFFT4_EINVAL); default 0           */
+    int32_t decode_cluster;  /* CTAs that decode one signal (a thread-block cluster of 1, 2,
+                                4, 8 or 16 CTAs sharing the update's buckets and the
+                                candidates); 0 (default) = the largest power of two up to 8
+                                with which the execute's decode CTAs fit on the SMs (one
+                                signal: 8; batches of 152 or more signals: 1).  The results
+                                do not depend on it                                         */
 } sfft4_opts;
 
 /* Fills *opts with the defaults above.  Returns SFFT4_EINVAL if opts is NULL. */
@@ -381,6 +387,20 @@ SFFT4_API int sfft4_profile_get(sfft4_plan_t plan, sfft4_profile* out, int32_t r
 SFFT4_API int sfft4_gather_probe(const void* x_dev, int32_t nsig, int64_t N, int64_t x_stride,
                                  float* sink_dev, int32_t blocks, int32_t iters,
                                  double* loads_per_second, void* stream);
+
+/*
+ * sfft4_gather_probe_ex -- sfft4_gather_probe with the knobs of a ceiling sweep: `threads` per
+ * CTA (32..1024, a multiple of 32), `inflight` independent loads per thread at a time (4, 8 or
+ * 16), and the L2 fetch granularity used during the measurement (l2_fetch_bytes 32, 64 or 128
+ * bytes, restored afterwards; 0 = the context's current limit).  The footprint is nsig x N x 8
+ * bytes: nsig = 1 keeps a 32 MB signal resident in L2, larger nsig exceed it.  The paper has
+ * no counterpart (it measures the device, not the method).
+ * Errors: SFFT4_EINVAL, SFFT4_ECUDA.
+ */
+SFFT4_API int sfft4_gather_probe_ex(const void* x_dev, int32_t nsig, int64_t N, int64_t x_stride,
+                                    float* sink_dev, int32_t blocks, int32_t threads, int32_t iters,
+                                    int32_t inflight, int32_t l2_fetch_bytes, double* loads_per_second,
+                                    void* stream);
 
 /*
  * sfft4_window_noalloc -- the flat window tables of sfft4_plan (G: 2h+1 float32

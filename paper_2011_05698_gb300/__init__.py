@@ -25,18 +25,20 @@ def load():
     return _lib.load()
 
 
-def gather_probe(xs, blocks=None, iters=64):
+def gather_probe(xs, blocks=None, iters=64, threads=512, inflight=4, l2_fetch_bytes=0):
     """Random 8-byte gathers per second within each row of xs (CUDA complex64, (nsig, N)):
-    the achievable rate of the gather's access pattern on this device."""
+    the achievable rate of the gather's access pattern on this device, with `threads` per CTA,
+    `inflight` loads per thread in flight (4, 8, 16) and the L2 fetch granularity (0 = as set)."""
     import torch
     lib = _lib.load()
     if blocks is None:
         blocks = torch.cuda.get_device_properties(xs.device).multi_processor_count * 8
     sink = torch.zeros(1, dtype=torch.float32, device=xs.device)
     out = ctypes.c_double()
-    check(lib.sfft4_gather_probe(ctypes.c_void_p(xs.data_ptr()), xs.shape[0], xs.shape[1], xs.stride(0),
-                                 ctypes.c_void_p(sink.data_ptr()), blocks, iters, ctypes.byref(out),
-                                 _stream_ptr(xs.device)), "sfft4_gather_probe")
+    check(lib.sfft4_gather_probe_ex(ctypes.c_void_p(xs.data_ptr()), xs.shape[0], xs.shape[1], xs.stride(0),
+                                    ctypes.c_void_p(sink.data_ptr()), blocks, threads, iters, inflight,
+                                    l2_fetch_bytes, ctypes.byref(out), _stream_ptr(xs.device)),
+          "sfft4_gather_probe_ex")
     return out.value
 
 
@@ -47,7 +49,8 @@ def _stream_ptr(device):
 
 def _opts(B1=0, delta=1e-8, precision="fp32", min_votes=0, select_factor=2.0, sig_floor=1e-10,
           mag_tol=0.5, max_iters=64, max_batch=1, trace=False, profile=False, graph=False,
-          location="multiscale", fold_order="signal_major", l2_fetch_bytes=0, trace_signal=0):
+          location="multiscale", fold_order="signal_major", l2_fetch_bytes=0, trace_signal=0,
+          decode_cluster=0):
     o = _lib.Opts()
     check(_lib.load().sfft4_opts_default(ctypes.byref(o)), "sfft4_opts_default")
     o.B1 = B1
@@ -67,6 +70,7 @@ def _opts(B1=0, delta=1e-8, precision="fp32", min_votes=0, select_factor=2.0, si
                     "iteration_major": _lib.SFFT4_FOLD_ITERATION_MAJOR}[fold_order]
     o.l2_fetch_bytes = l2_fetch_bytes
     o.trace_signal = trace_signal
+    o.decode_cluster = decode_cluster
     return o
 
 
@@ -86,12 +90,14 @@ class Plan:
     def __init__(self, N, K, l=16, q=1.0, seed=0, *, B1=0, delta=1e-8, precision="fp32",
                  min_votes=0, select_factor=2.0, sig_floor=1e-10, mag_tol=0.5, max_iters=64,
                  max_batch=1, trace=False, profile=False, graph=False, location="multiscale",
-                 fold_order="signal_major", l2_fetch_bytes=0, trace_signal=0, device=None):
+                 fold_order="signal_major", l2_fetch_bytes=0, trace_signal=0, decode_cluster=0,
+                 device=None):
         import torch
         lib = _lib.load()
         self.device = _device(device)
         o = _opts(B1, delta, precision, min_votes, select_factor, sig_floor, mag_tol, max_iters,
-                  max_batch, trace, profile, graph, location, fold_order, l2_fetch_bytes, trace_signal)
+                  max_batch, trace, profile, graph, location, fold_order, l2_fetch_bytes, trace_signal,
+                  decode_cluster)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             check(lib.sfft4_plan(ctypes.byref(h), N, K, l, q, seed, ctypes.byref(o)), "sfft4_plan")

@@ -28,7 +28,8 @@ class Opts(ctypes.Structure):
                 ("max_iters", ctypes.c_int32), ("max_batch", ctypes.c_int32),
                 ("trace", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("l2_fetch_bytes", ctypes.c_int32), ("graph", ctypes.c_int32), ("location", ctypes.c_int32),
-                ("fold_order", ctypes.c_int32), ("trace_signal", ctypes.c_int32)]
+                ("fold_order", ctypes.c_int32), ("trace_signal", ctypes.c_int32),
+                ("decode_cluster", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -99,6 +100,9 @@ SIGNATURES = [
     ("sfft4_profile_get", ctypes.c_int, [_P, ctypes.POINTER(Profile), ctypes.c_int32]),
     ("sfft4_gather_probe", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _P,
                                           ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), _P]),
+    ("sfft4_gather_probe_ex", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _P,
+                                             ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.c_int32, ctypes.POINTER(ctypes.c_double), _P]),
     ("sfft4_window_noalloc", ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_double, _P,
                                             ctypes.c_int64, _P, ctypes.c_int64, _P]),
     ("sfft4_sync_status", ctypes.c_int, [_P]),

@@ -19,7 +19,11 @@
 #include <atomic>
 #include <mutex>
 
+#include <cooperative_groups.h>
+
 #include "sfft4_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace sfft4 {
 
@@ -547,12 +551,36 @@ __device__ uint32_t block_radix_select(const float* key, int b_lo, int b_hi, int
     return prefix;
 }
 
-// One CTA per signal: update the bucket arrays by the found set, select the large
-// buckets, locate each candidate by the multiscale method, vote, estimate and merge.
-// All modular arithmetic is exact in 32 bits (N = 2^n divides 2^32).  RMAX bounds the
-// rounds R of the iteration (16, or 64 for extreme (l, q)).
+// Barrier of the CTAs that decode one signal: the block itself, or (csize > 1) the thread-block
+// cluster, after making this block's global writes (bucket updates) visible to the others.
+__device__ __forceinline__ void decode_sync(int csize) {
+    if (csize > 1) {
+        __threadfence();
+        cg::this_cluster().sync();
+    } else {
+        __syncthreads();
+    }
+}
+
+// Contiguous share [lo, hi) of n items of rank r among c ranks.
+__device__ __forceinline__ void rank_share(int n, int r, int c, int* lo, int* hi) {
+    *lo = (int)((int64_t)n * r / c);
+    *hi = (int)((int64_t)n * (r + 1) / c);
+}
+
+// One CTA per signal, or a cluster of csize CTAs (rank crank) per signal: update the bucket
+// arrays by the found set, select the large buckets, locate each candidate by the multiscale
+// method, vote, estimate and merge.  All modular arithmetic is exact in 32 bits (N = 2^n
+// divides 2^32).  RMAX bounds the rounds R of the iteration (16, or 64 for extreme (l, q)).
+// In a cluster every rank stages the found set and selects the candidates itself (the same
+// deterministic steps, so the same results); the update's buckets (gather form) or found
+// entries (scatter form, with the int64 sums of all ranks added through distributed shared
+// memory) and the candidates' location and estimation are split into contiguous shares; rank
+// 0 gathers the candidates' results and merges.  Each item is computed exactly as by one CTA,
+// so the outputs do not depend on csize.
 template <int RMAX>
-__device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig) {
+__device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig, const int crank = 0,
+                                            const int csize = 1) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ uint32_t s_par[3];
     __shared__ int s_ws[33];
@@ -701,6 +729,9 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig) 
                     __syncthreads();
                 }
             }
+            int b_lo, b_hi;
+            rank_share(B, crank, csize, &b_lo, &b_hi);
+            const int Bc = b_hi - b_lo;
             for (int r0 = 0; r0 < R; r0 += kUpdRounds) {
                 const int nr = min(kUpdRounds, R - r0);
                 // round-major (ec[rr F0 + j]): the entries a warp gathers below fall in
@@ -717,8 +748,8 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig) 
                     }
                 }
                 __syncthreads();
-                for (int item = tid; item < B * splits; item += T) {
-                    const int bp = item % B, sp = item / B;
+                for (int item = tid; item < Bc * splits; item += T) {
+                    const int bp = b_lo + item % Bc, sp = item / Bc;
                     // the item's few entries add in FP32 in their staged (fixed) order; the
                     // items' sums then add exactly in int64
                     float fr[kUpdRounds], fi[kUpdRounds];
@@ -769,8 +800,8 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig) 
                 }
                 if (splits > 1) {
                     __syncthreads();
-                    for (int e = tid; e < nr * B; e += T) {
-                        const int rr = e / B, b = e - rr * B;
+                    for (int e = tid; e < nr * Bc; e += T) {
+                        const int rr = e / Bc, b = b_lo + e - rr * Bc;
                         long long sr = 0, si = 0;
                         for (int sp = 0; sp < splits; ++sp) {
                             const long long* pp = part + 2 * ((size_t)(sp * kUpdRounds + rr) * B + b);
@@ -795,11 +826,15 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig) 
             int nco = (int)((size_t)(T >> 5) < ncmax ? (size_t)(T >> 5) : ncmax);
             if (nco < 1) nco = 1;
             long long* wacc = acc + (size_t)((tid >> 5) % nco) * rc * per_round;
+            int e_lo, e_hi, b_lo, b_hi;
+            rank_share(F0, crank, csize, &e_lo, &e_hi);
+            rank_share(B, crank, csize, &b_lo, &b_hi);
+            const int Bc = b_hi - b_lo;
             for (int r0 = 0; r0 < R; r0 += rc) {
                 const int nr = min(rc, R - r0);
                 for (int i = tid; i < nco * rc * per_round; i += T) acc[i] = 0;
                 __syncthreads();
-                for (int i = tid; i < F0; i += T) {
+                for (int i = e_lo + tid; i < e_hi; i += T) {
                     const uint32_t f = (uint32_t)ff[i];
                     const double2 vd = fv[i];
                     const float2 v = make_float2((float)vd.x, (float)vd.y);
@@ -824,14 +859,18 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig) 
                         }
                     }
                 }
-                __syncthreads();
-                for (int e = tid; e < nr * B; e += T) {
-                    const int rr = e / B, b = e - rr * B;
+                decode_sync(csize);  // every rank's copies are complete
+                for (int e = tid; e < nr * Bc; e += T) {
+                    const int rr = e / Bc, b = b_lo + e - rr * Bc;
                     long long sr = 0, si = 0;
-                    for (int w = 0; w < nco; ++w) {
-                        const long long* aw = acc + ((size_t)w * rc + rr) * per_round;
-                        sr += aw[2 * b];
-                        si += aw[2 * b + 1];
+                    for (int q = 0; q < csize; ++q) {
+                        // the copies of rank q (this block's own when csize == 1)
+                        const long long* aq = csize > 1 ? cg::this_cluster().map_shared_rank(acc, q) : acc;
+                        for (int w = 0; w < nco; ++w) {
+                            const long long* aw = aq + ((size_t)w * rc + rr) * per_round;
+                            sr += aw[2 * b];
+                            si += aw[2 * b + 1];
+                        }
                     }
                     float2* yp = &Y[(int64_t)(r0 + rr) * B + b];
                     float2 yv = *yp;
@@ -839,15 +878,18 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig) 
                     yv.y -= ll2f_rn(si) * iscale;
                     *yp = yv;
                 }
-                __syncthreads();
+                decode_sync(csize);  // no rank clears its copies while another still reads them
             }
         }
     }
 
     // ---- 2. large-bucket selection (Section 3: buckets with p >= 1) -------------------
+    // (a cluster's ranks updated disjoint buckets: all of them are visible after this barrier;
+    // the bucket rows are read past L1 from here on)
+    if (csize > 1) decode_sync(csize);
     float mx = 0.f;
     for (int b = tid; b < B; b += T) {
-        const float2 y0 = Y[b];
+        const float2 y0 = __ldcg(Y + b);
         const float k2 = fmaf(y0.x, y0.x, y0.y * y0.y);
         key[b] = k2;
         mx = fmaxf(mx, k2);
@@ -861,8 +903,10 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig) 
             const float th = a.sig_floor > 0.f ? a.sig_floor * m : -1.f;
             int e = 0;
             frexpf(sqrtf(m), &e);
-            a.theta[sig] = th;
-            a.fxexp[sig] = e;
+            if (crank == 0) {
+                a.theta[sig] = th;
+                a.fxexp[sig] = e;
+            }
             s_theta = th;
         }
     } else if (tid == 0) {
@@ -932,9 +976,11 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig) 
     // ---- 3. multiscale location, votes, estimation: one thread per candidate ----------
     const int l = a.l;
     const int need = a.min_votes > 0 ? min(a.min_votes, S) : S;
-    for (int ci = tid; ci < ncand; ci += T) {
+    int r_lo, r_hi;  // this rank's share of the candidates
+    rank_share(ncand, crank, csize, &r_lo, &r_hi);
+    for (int ci = r_lo + tid; ci < r_hi; ci += T) {
         const int b = cand[ci];
-        const float2 y0 = Y[b];
+        const float2 y0 = __ldcg(Y + b);
         const float m0 = fmaf(y0.x, y0.x, y0.y * y0.y);
         // phases phi_s (2^-32 turns) and magnitude votes of all levels, loaded up front
         uint32_t ph[RMAX];
@@ -942,7 +988,7 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig) 
 #pragma unroll
         for (int s = 1; s < RMAX; ++s) {
             if (s <= S) {
-                const float2 ys = Y[(int64_t)s * B + b];
+                const float2 ys = __ldcg(Y + (int64_t)s * B + b);
                 ph[s - 1] = phase_fixed(ys, y0);
                 const float ms = fmaf(ys.x, ys.x, ys.y * ys.y);
                 magok |= (fabsf(ms - m0) <= a.mag_tol * m0) ? (1ull << (s - 1)) : 0ull;
@@ -975,7 +1021,7 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig) 
             if (s == S) phS = ph[s - 1];
         if (a.fine_phase) {
             // phase step 1/N: FP32 atan2 is too coarse past N ~ 2^20
-            phS = phase_fixed64(Y[(int64_t)S * B + b], y0);
+            phS = phase_fixed64(__ldcg(Y + (int64_t)S * B + b), y0);
 #pragma unroll
             for (int s = 1; s < RMAX; ++s)
                 if (s == S) ph[s - 1] = phS;
@@ -1020,7 +1066,7 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig) 
                 if (r < R) {
                     const uint32_t o_r = (aoff + sigma * (uint32_t)it->tau[r]) & mask;
                     const float2 e = cis_2pi_frac((f * o_r) & mask, n);
-                    const float2 v = cmul(Y[(int64_t)r * B + b], make_float2(e.x, -e.y));
+                    const float2 v = cmul(__ldcg(Y + (int64_t)r * B + b), make_float2(e.x, -e.y));
                     vre[r] = v.x * ig;
                     vim[r] = v.y * ig;
                 }
@@ -1032,6 +1078,28 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig) 
         }
     }
     __syncthreads();
+    if (csize > 1) {
+        // rank 0 copies the other ranks' candidate results (their shares of cf, cv, cvt)
+        decode_sync(csize);
+        if (crank == 0) {
+            for (int q = 1; q < csize; ++q) {
+                int q_lo, q_hi;
+                rank_share(ncand, q, csize, &q_lo, &q_hi);
+                const int32_t* rf = cg::this_cluster().map_shared_rank(cf, q);
+                const float2* rv = cg::this_cluster().map_shared_rank(cv, q);
+                const int8_t* rt = cg::this_cluster().map_shared_rank(cvt, q);
+                for (int ci = q_lo + tid; ci < q_hi; ci += T) {
+                    cvt[ci] = rt[ci];
+                    if (rt[ci] >= 0) {
+                        cf[ci] = rf[ci];
+                        cv[ci] = rv[ci];
+                    }
+                }
+            }
+        }
+        decode_sync(csize);  // the other ranks' shared memory is no longer read
+        if (crank != 0) return;
+    }
 
     // ---- 4. merge: x^m = x^{m-1} + x'^m (Section 3.1, step 5) -------------------------
     for (int ci = tid; ci < ncand; ci += T)
@@ -1064,6 +1132,15 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig) 
 template <int RMAX>
 __global__ void __launch_bounds__(kDecodeThreads, 2) k_decode(const DecodeArgs a) {
     decode_body<RMAX>(a, blockIdx.x);
+}
+
+// The decode of each signal spread over a thread-block cluster (launched with a cluster
+// dimension of csize along x; cluster c decodes signal c): the one-signal latency path.
+template <int RMAX>
+__global__ void __launch_bounds__(kDecodeThreads, 2) k_decode_cluster(const DecodeArgs a) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int csize = (int)cl.num_blocks();
+    decode_body<RMAX>(a, blockIdx.x / csize, (int)cl.block_rank(), csize);
 }
 
 // Batch of signals with different N and K: CTA b decodes signal jobs[list[b]], whose
@@ -1328,6 +1405,16 @@ DecodeArgs make_decode_args(const sfft4_plan_s* p, int mi) {
     return a;
 }
 
+// CTAs per signal of the decode: opts.decode_cluster, or (0) the largest power of two up to 8
+// with which the batch's decode CTAs still fit on the SMs, so that a small batch spreads each
+// signal's decode over several SMs instead of leaving them idle.
+int decode_cluster_size(const sfft4_plan_s* p, int nsig) {
+    if (p->o.decode_cluster > 0) return p->o.decode_cluster;
+    int c = 8;
+    while (c > 1 && (int64_t)nsig * c > p->sm_count) c >>= 1;
+    return c;
+}
+
 int launch_decode(sfft4_plan_s* p, int mi, int nsig, cudaStream_t st) {
     int rc0 = configure_kernels();
     if (rc0) return rc0;
@@ -1337,10 +1424,29 @@ int launch_decode(sfft4_plan_s* p, int mi, int nsig, cudaStream_t st) {
     cudaEvent_t ev = nullptr;
     int rc = prof_begin(p, st, &ev);
     if (rc) return rc;
-    if (d.R <= 8) k_decode<8><<<nsig, kDecodeThreads, smem, st>>>(a);
-    else if (d.R <= 16) k_decode<16><<<nsig, kDecodeThreads, smem, st>>>(a);
-    else k_decode<64><<<nsig, kDecodeThreads, smem, st>>>(a);
-    rc = check_cuda(cudaGetLastError());
+    const int C = decode_cluster_size(p, nsig);
+    if (C > 1) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(nsig * C));
+        cfg.blockDim = dim3(kDecodeThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (d.R <= 8) rc = check_cuda(cudaLaunchKernelEx(&cfg, k_decode_cluster<8>, a));
+        else if (d.R <= 16) rc = check_cuda(cudaLaunchKernelEx(&cfg, k_decode_cluster<16>, a));
+        else rc = check_cuda(cudaLaunchKernelEx(&cfg, k_decode_cluster<64>, a));
+    } else {
+        if (d.R <= 8) k_decode<8><<<nsig, kDecodeThreads, smem, st>>>(a);
+        else if (d.R <= 16) k_decode<16><<<nsig, kDecodeThreads, smem, st>>>(a);
+        else k_decode<64><<<nsig, kDecodeThreads, smem, st>>>(a);
+        rc = check_cuda(cudaGetLastError());
+    }
     if (rc) return rc;
     return prof_end(p, st, ev, kProfDecode, 0);
 }
@@ -1580,6 +1686,13 @@ int configure_kernels() {
                                                   (int)decode_smem(kBMax)));
     if (!rc) rc = check_cuda(cudaFuncSetAttribute(k_decode<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   (int)decode_smem(kBMax)));
+    const void* decs_c[] = {(const void*)k_decode_cluster<8>, (const void*)k_decode_cluster<16>,
+                            (const void*)k_decode_cluster<64>};
+    for (const void* f : decs_c) {
+        if (!rc) rc = check_cuda(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)decode_smem(kBMax)));
+        if (!rc) rc = check_cuda(cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    }
     if (!rc) rc = check_cuda(cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   8 * kKMax));
     if (!rc) rc = configure_dft_tc();
