@@ -424,8 +424,11 @@ constexpr int kGatherMaxB = 512;
 // Dynamic shared memory of k_decode for B buckets: 26 B bytes of per-bucket arrays, and at
 // least 108 KB for the update (staged found entries, 24 B each, or accumulator copies).  Two
 // 512-thread CTAs fit on an SM.
+__host__ __device__ inline size_t decode_tables_off(int B) { return (26 * (size_t)B + 15) & ~(size_t)15; }
 __host__ __device__ inline size_t decode_smem(int B) {
-    const size_t base = 26 * (size_t)B;
+    // the location's block-centre and region-shift tables (at most 63 block levels x 32 blocks
+    // x 8 bytes) follow the per-bucket arrays
+    const size_t base = decode_tables_off(B) + (size_t)(kMaxRounds - 1) * 32 * 8;
     const size_t upd = 108 * 1024;
     return base > upd ? base : upd;
 }
@@ -495,17 +498,23 @@ __device__ __noinline__ uint32_t phase_fixed64(float2 ys, float2 y0) {
 // Radix select over 32-bit keys held one chunk per thread: returns the value T of the
 // n-th largest key (1 <= n <= count) by four passes over 8-bit digits, most significant
 // first.  hist must hold 256 ints of shared memory; all threads of the block call it.
-__device__ uint32_t block_radix_select(const float* key, int b_lo, int b_hi, int n, int* hist,
+__device__ uint32_t block_radix_select(const float* key, int b_lo, int b_hi, int E, int n, int* hist,
                                        int* s_bcast) {
+    // hist holds two 256-bin histograms and s_bcast two (digit, rank) pairs, used by
+    // alternate passes: a pass counts into one histogram while the other is cleared for the
+    // next, so each pass needs two barriers
     uint32_t prefix = 0, pmask = 0;
     int rank = n;  // rank of the wanted key among keys matching the prefix (1 = largest)
+    for (int i = threadIdx.x; i < 512; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
     for (int d = 3; d >= 0; --d) {
-        for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
-        __syncthreads();
+        int* H = hist + 256 * (d & 1);
+        int* Hn = hist + 256 * ((d & 1) ^ 1);
+        int* bc = s_bcast + 2 * (d & 1);
         // warp-aggregated: lanes holding the same digit add once (keys cluster in a few
-        // exponent bins, so plain atomics would serialise on those bins)
-        constexpr int kChunkMax = (kBMax + kDecodeThreads - 1) / kDecodeThreads;
-        for (int e = 0; e < kChunkMax; ++e) {
+        // exponent bins, so plain atomics would serialise on those bins); E, the chunk length,
+        // is the same in every thread, so all lanes take part in each match
+        for (int e = 0; e < E; ++e) {
             const int b = b_lo + e;
             int digit = 256;
             if (b < b_hi) {
@@ -514,7 +523,7 @@ __device__ uint32_t block_radix_select(const float* key, int b_lo, int b_hi, int
             }
             const unsigned peers = __match_any_sync(0xffffffffu, digit);
             if (digit < 256 && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1))
-                atomicAdd(&hist[digit], __popc(peers));
+                atomicAdd(&H[digit], __popc(peers));
         }
         __syncthreads();
         if (threadIdx.x < 32) {
@@ -522,7 +531,7 @@ __device__ uint32_t block_radix_select(const float* key, int b_lo, int b_hi, int
             const int lane = threadIdx.x;
             int loc[8], tot = 0;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) { loc[q] = hist[255 - 8 * lane - q]; tot += loc[q]; }
+            for (int q = 0; q < 8; ++q) { loc[q] = H[255 - 8 * lane - q]; tot += loc[q]; }
             int incl = tot;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -535,19 +544,21 @@ __device__ uint32_t block_radix_select(const float* key, int b_lo, int b_hi, int
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     if (c < rank && rank <= c + loc[q]) {
-                        s_bcast[0] = 255 - 8 * lane - q;
-                        s_bcast[1] = rank - c;
+                        bc[0] = 255 - 8 * lane - q;
+                        bc[1] = rank - c;
                     }
                     c += loc[q];
                 }
             }
+        } else {
+            for (int i = threadIdx.x - 32; i < 256; i += blockDim.x - 32) Hn[i] = 0;
         }
         __syncthreads();
-        prefix |= (uint32_t)s_bcast[0] << (8 * d);
+        prefix |= (uint32_t)bc[0] << (8 * d);
         pmask |= 255u << (8 * d);
-        rank = s_bcast[1];
-        __syncthreads();
+        rank = bc[1];
     }
+    __syncthreads();
     return prefix;
 }
 
@@ -584,12 +595,19 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig, 
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ uint32_t s_par[3];
     __shared__ int s_ws[33];
-    __shared__ int s_hist[256];
-    __shared__ int s_bc[2];
+    __shared__ int s_hist[512];
+    __shared__ int s_bc[4];
     __shared__ int s_cnt;
     __shared__ unsigned s_max;
     __shared__ float s_theta;
     __shared__ int s_fx;
+    // the iteration's tables the location reads level by level (a chain of dependent loads per
+    // candidate), copied to shared memory: offsets, vote thresholds and phase scales here, the
+    // block centres and region shifts (l per block level) after the update, past the bucket
+    // arrays of the selection and location (decode_smem leaves room for them)
+    __shared__ uint32_t s_tau[RMAX];
+    __shared__ uint32_t s_H[RMAX];
+    __shared__ float s_jscale[RMAX];
     const IterDev* __restrict__ it = a.it;
     const int tid = threadIdx.x, T = blockDim.x;
     const int B = it->B, R = it->R, S = it->S, logL = it->logL;
@@ -602,6 +620,13 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig, 
     int8_t* fvotes = a.fvotes + (int64_t)sig * a.Fcap;
     int32_t* hk = a.hkeys + ((int64_t)sig << a.Hlog);
     int32_t* hv = a.hvals + ((int64_t)sig << a.Hlog);
+    for (int i = tid; i < R; i += T) {
+        s_tau[i] = (uint32_t)it->tau[i];
+        if (i < S) {
+            s_H[i] = it->H[i];
+            s_jscale[i] = it->jscale[i];
+        }
+    }
     if (tid == 0) {
         uint64_t s, o;
         permutation_draw(a.seed, (uint64_t)(a.signal0 + sig), (uint64_t)it->m, a.N, &s, &o);
@@ -667,9 +692,12 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig, 
             long long* part = (long long*)(smraw + acc_off);
             for (int b = tid; b <= B; b += T) cnt[b] = 0;
             __syncthreads();
+            int* tb = (int*)(smraw + off_c);  // each entry's bucket (area of the rotated values)
             for (int e = tid; e < F0; e += T) {
                 const uint32_t u = (sigma * (uint32_t)ff[e]) & mask;
-                atomicAdd(&cnt[(((u + (L >> 1)) >> logL) & (uint32_t)(B - 1))], 1);
+                const int b0 = (int)(((u + (L >> 1)) >> logL) & (uint32_t)(B - 1));
+                tb[e] = b0;
+                atomicAdd(&cnt[b0], 1);
             }
             __syncthreads();
             {
@@ -688,45 +716,97 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig, 
                 if (tid == 0) cnt[B] = tot;
             }
             __syncthreads();
-            // stable placement: within a bucket, entries keep their found-set order (ranks from
-            // warp matches, the warps of a chunk taking their turn in order), so that each item
-            // below adds its entries in a fixed order
+            // stable placement: within a bucket, entries keep their found-set order, so that each
+            // item below adds its entries in a fixed order.  Warp w takes a contiguous share of
+            // the entries and counts them per bucket (ranks among equal buckets from warp
+            // matches); an exclusive scan over the warps of each bucket then gives every entry
+            // its place.  The per-warp counts go past the staged entries, each entry's bucket and
+            // rank in its warp's share into the area of the rotated values (unused until the
+            // passes below).
             const int lane = tid & 31, wid = tid >> 5, nw = (T + 31) >> 5;
-            for (int c0 = 0; c0 < F0; c0 += T) {
-                const int e = c0 + tid;
-                const bool has = e < F0;
-                uint32_t f = 0;
-                float2 ve = make_float2(0.f, 0.f);
-                int b0 = B + lane;  // a key of its own for lanes without an entry
-                float g3[3] = {0.f, 0.f, 0.f};
-                if (has) {
-                    f = (uint32_t)ff[e];
+            int* M = (int*)(smraw + acc_off);  // [nw][B]
+            if (acc_off + (size_t)4 * nw * B <= decode_smem(B)) {
+                int* tr = tb + F0;
+                const int chunk = ((F0 + nw - 1) / nw + 31) & ~31;
+                for (int i = tid; i < nw * B; i += T) M[i] = 0;
+                __syncthreads();
+                const int e0 = min(F0, wid * chunk), e1 = min(F0, e0 + chunk);
+                int* Mw = M + wid * B;
+                for (int c0 = e0; c0 < e1; c0 += 32) {
+                    const int e = c0 + lane;
+                    const bool has = e < e1;
+                    const int b0 = has ? tb[e] : B + lane;  // a key of its own without an entry
+                    const unsigned grp = __match_any_sync(0xffffffffu, b0);
+                    const int rank = __popc(grp & ((1u << lane) - 1u));
+                    if (has) tr[e] = Mw[b0] + rank;
+                    __syncwarp();
+                    if (has && rank == 0) Mw[b0] += __popc(grp);
+                    __syncwarp();
+                }
+                __syncthreads();
+                for (int bb = tid; bb < B; bb += T) {
+                    int run = cnt[bb];
+                    for (int w = 0; w < nw; ++w) {
+                        const int t = M[w * B + bb];
+                        M[w * B + bb] = run;
+                        run += t;
+                    }
+                }
+                __syncthreads();
+                for (int e = tid; e < F0; e += T) {
+                    const uint32_t f = (uint32_t)ff[e];
                     const double2 vd = fv[e];
-                    ve = make_float2((float)vd.x, (float)vd.y);
                     const uint32_t u = (sigma * f) & mask;
-                    b0 = (int)(((u + (L >> 1)) >> logL) & (uint32_t)(B - 1));
+                    const int b0 = tb[e];
+                    const int pos = M[(e / chunk) * B + b0] + tr[e];
+                    ev[pos] = make_float2((float)vd.x, (float)vd.y);
+                    ef[pos] = f;
 #pragma unroll
                     for (int q = 0; q < 3; ++q) {
                         const int bb = (b0 + q - 1) & (B - 1);
                         const int k = (int)((((uint32_t)bb * L - u) + halfN) & mask) - (int)halfN;
-                        g3[q] = it->Ghat[k < 0 ? -k : k] * scale;
+                        eg[3 * pos + q] = it->Ghat[k < 0 ? -k : k] * scale;
                     }
                 }
-                const unsigned grp = __match_any_sync(0xffffffffu, b0);
-                const int rank = __popc(grp & ((1u << lane) - 1u));
-                for (int w = 0; w < nw; ++w) {
-                    if (wid == w) {
-                        if (has) {
-                            const int pos = fillp[b0] + rank;
-                            ev[pos] = ve;
-                            ef[pos] = f;
-#pragma unroll
-                            for (int q = 0; q < 3; ++q) eg[3 * pos + q] = g3[q];
+                __syncthreads();
+            } else {
+                // the warps of a chunk take their turn in order
+                for (int c0 = 0; c0 < F0; c0 += T) {
+                    const int e = c0 + tid;
+                    const bool has = e < F0;
+                    uint32_t f = 0;
+                    float2 ve = make_float2(0.f, 0.f);
+                    int b0 = B + lane;  // a key of its own for lanes without an entry
+                    float g3[3] = {0.f, 0.f, 0.f};
+                    if (has) {
+                        f = (uint32_t)ff[e];
+                        const double2 vd = fv[e];
+                        ve = make_float2((float)vd.x, (float)vd.y);
+                        const uint32_t u = (sigma * f) & mask;
+                        b0 = (int)(((u + (L >> 1)) >> logL) & (uint32_t)(B - 1));
+    #pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            const int bb = (b0 + q - 1) & (B - 1);
+                            const int k = (int)((((uint32_t)bb * L - u) + halfN) & mask) - (int)halfN;
+                            g3[q] = it->Ghat[k < 0 ? -k : k] * scale;
                         }
-                        __syncwarp();
-                        if (has && rank == 0) fillp[b0] += __popc(grp);
                     }
-                    __syncthreads();
+                    const unsigned grp = __match_any_sync(0xffffffffu, b0);
+                    const int rank = __popc(grp & ((1u << lane) - 1u));
+                    for (int w = 0; w < nw; ++w) {
+                        if (wid == w) {
+                            if (has) {
+                                const int pos = fillp[b0] + rank;
+                                ev[pos] = ve;
+                                ef[pos] = f;
+    #pragma unroll
+                                for (int q = 0; q < 3; ++q) eg[3 * pos + q] = g3[q];
+                            }
+                            __syncwarp();
+                            if (has && rank == 0) fillp[b0] += __popc(grp);
+                        }
+                        __syncthreads();
+                    }
                 }
             }
             int b_lo, b_hi;
@@ -742,7 +822,7 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig, 
 #pragma unroll
                     for (int rr = 0; rr < kUpdRounds; ++rr) {
                         if (rr < nr) {
-                            const uint32_t o_r = (aoff + sigma * (uint32_t)it->tau[r0 + rr]) & mask;
+                            const uint32_t o_r = (aoff + sigma * s_tau[r0 + rr]) & mask;
                             ec[rr * F0 + pos] = cmul(v, cis_2pi_frac((f * o_r) & mask, n));
                         }
                     }
@@ -849,7 +929,7 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig, 
                         g3[q] = it->Ghat[k < 0 ? -k : k] * scale;
                     }
                     for (int rr = 0; rr < nr; ++rr) {
-                        const uint32_t o_r = (aoff + sigma * (uint32_t)it->tau[r0 + rr]) & mask;
+                        const uint32_t o_r = (aoff + sigma * s_tau[r0 + rr]) & mask;
                         const float2 c = cmul(v, cis_2pi_frac((f * o_r) & mask, n));
                         long long* ar = wacc + (size_t)rr * per_round;
     #pragma unroll
@@ -887,6 +967,14 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig, 
     // (a cluster's ranks updated disjoint buckets: all of them are visible after this barrier;
     // the bucket rows are read past L1 from here on)
     if (csize > 1) decode_sync(csize);
+    const int lb = a.l;
+    uint32_t* s_Cj = (uint32_t*)(smraw + decode_tables_off(B));  // [S - 1][l]
+    int32_t* s_Dj = (int32_t*)(s_Cj + (S - 1) * lb);              // [S - 1][l]
+    for (int i = tid; i < (S - 1) * lb; i += T) {
+        const int lv = i / lb, j = i - lv * lb;
+        s_Cj[i] = it->Cj[lv][j];
+        s_Dj[i] = it->Dj[lv][j];
+    }
     float mx = 0.f;
     for (int b = tid; b < B; b += T) {
         const float2 y0 = __ldcg(Y + b);
@@ -944,7 +1032,7 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig, 
         int need_ties = 0;
         if (n_c < B) {
             // T = the n_c-th largest key (keys >= 0 compare as unsigned integers)
-            Tb = block_radix_select(key, b_lo, b_hi, n_c, s_hist, s_bc);
+            Tb = block_radix_select(key, b_lo, b_hi, E, n_c, s_hist, s_bc);
             int gt = 0;
             for (int b = b_lo; b < b_hi; ++b) gt += (__float_as_uint(key[b]) > Tb);
             need_ties = n_c - block_count(gt, &s_cnt);
@@ -999,19 +1087,19 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig, 
 #pragma unroll
         for (int s = 1; s < RMAX; ++s) {
             if (s < S) {
-                const uint32_t ts = (uint32_t)it->tau[s];
+                const uint32_t ts = s_tau[s];
                 const uint32_t Ap = ((uint32_t)umin * ts) << shift;
-                const int j0 = (int)floorf((float)(ph[s - 1] - Ap) * it->jscale[s - 1]);
+                const int j0 = (int)floorf((float)(ph[s - 1] - Ap) * s_jscale[s - 1]);
                 uint32_t bd = 0xffffffffu;
                 int bj = l;
 #pragma unroll
                 for (int q = 0; q < 7; ++q) {
                     const int j = q < 5 ? j0 - 2 + q : (q == 5 ? 0 : l - 1);
                     if (j < 0 || j >= l) continue;
-                    const uint32_t d = circ_dist(ph[s - 1], Ap + it->Cj[s - 1][j]);
+                    const uint32_t d = circ_dist(ph[s - 1], Ap + s_Cj[(s - 1) * lb + j]);
                     if (d < bd || (d == bd && j < bj)) { bd = d; bj = j; }
                 }
-                umin += it->Dj[s - 1][bj];
+                umin += s_Dj[(s - 1) * lb + bj];
             }
         }
         // final level: the Lbar_S integers u_min + i
@@ -1028,11 +1116,11 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig, 
         }
         uint32_t ustar;
         {
-            const uint32_t ts = (uint32_t)it->tau[S];
+            const uint32_t ts = s_tau[S];
             const int Lb = (int)it->Lbar[S - 1];
             const uint32_t Dl = (uint32_t)it->W[S - 1];
             const uint32_t P0 = ((uint32_t)umin * ts) << shift;
-            const int i0 = (int)floorf((float)(phS - P0) * it->jscale[S - 1]);
+            const int i0 = (int)floorf((float)(phS - P0) * s_jscale[S - 1]);
             uint32_t bd = 0xffffffffu;
             int bi = Lb;
 #pragma unroll
@@ -1049,8 +1137,8 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig, 
 #pragma unroll
         for (int s = 1; s < RMAX; ++s) {
             if (s <= S) {
-                const uint32_t Ps = (ustar * (uint32_t)it->tau[s]) << shift;
-                nv += (circ_dist(ph[s - 1], Ps) <= it->H[s - 1]) && ((magok >> (s - 1)) & 1ull);
+                const uint32_t Ps = (ustar * s_tau[s]) << shift;
+                nv += (circ_dist(ph[s - 1], Ps) <= s_H[s - 1]) && ((magok >> (s - 1)) & 1ull);
             }
         }
         const bool own = (int)(((ustar + (L >> 1)) >> logL) & (uint32_t)(B - 1)) == b;
@@ -1064,7 +1152,7 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig, 
 #pragma unroll
             for (int r = 0; r < RMAX; ++r) {
                 if (r < R) {
-                    const uint32_t o_r = (aoff + sigma * (uint32_t)it->tau[r]) & mask;
+                    const uint32_t o_r = (aoff + sigma * s_tau[r]) & mask;
                     const float2 e = cis_2pi_frac((f * o_r) & mask, n);
                     const float2 v = cmul(__ldcg(Y + (int64_t)r * B + b), make_float2(e.x, -e.y));
                     vre[r] = v.x * ig;
@@ -1079,25 +1167,22 @@ __device__ __forceinline__ void decode_body(const DecodeArgs& a, const int sig, 
     }
     __syncthreads();
     if (csize > 1) {
-        // rank 0 copies the other ranks' candidate results (their shares of cf, cv, cvt)
-        decode_sync(csize);
-        if (crank == 0) {
-            for (int q = 1; q < csize; ++q) {
-                int q_lo, q_hi;
-                rank_share(ncand, q, csize, &q_lo, &q_hi);
-                const int32_t* rf = cg::this_cluster().map_shared_rank(cf, q);
-                const float2* rv = cg::this_cluster().map_shared_rank(cv, q);
-                const int8_t* rt = cg::this_cluster().map_shared_rank(cvt, q);
-                for (int ci = q_lo + tid; ci < q_hi; ci += T) {
-                    cvt[ci] = rt[ci];
-                    if (rt[ci] >= 0) {
-                        cf[ci] = rf[ci];
-                        cv[ci] = rv[ci];
-                    }
+        // the other ranks store their shares of the candidate results (cf, cv, cvt) into rank
+        // 0's arrays (those indices are rank 0's only after the update, which every rank has
+        // finished: the selection began with a cluster barrier)
+        if (crank != 0) {
+            int32_t* rf = cg::this_cluster().map_shared_rank(cf, 0);
+            float2* rv = cg::this_cluster().map_shared_rank(cv, 0);
+            int8_t* rt = cg::this_cluster().map_shared_rank(cvt, 0);
+            for (int ci = r_lo + tid; ci < r_hi; ci += T) {
+                rt[ci] = cvt[ci];
+                if (cvt[ci] >= 0) {
+                    rf[ci] = cf[ci];
+                    rv[ci] = cv[ci];
                 }
             }
         }
-        decode_sync(csize);  // the other ranks' shared memory is no longer read
+        decode_sync(csize);  // rank 0 holds every candidate's result
         if (crank != 0) return;
     }
 
