@@ -53,6 +53,8 @@ extern "C" {
 #define SFFT4_LOC_TWO_ROUND 1
 #define SFFT4_FOLD_SIGNAL_MAJOR 0     /* sfft4_opts.fold_order */
 #define SFFT4_FOLD_ITERATION_MAJOR 1
+#define SFFT4_BATCH_PERSISTENT 0      /* sfft4_opts.batch_exec */
+#define SFFT4_BATCH_LEVELS 1
 
 typedef struct sfft4_plan_s* sfft4_plan_t;   /* opaque, library-owned */
 
@@ -110,6 +112,15 @@ typedef struct {
                                 bucket arrays and found sets sfft4_trace_get returns (0 <=
                                 trace_signal < max_batch; an execute of fewer signals than
                                 trace_signal + 1 returns SFFT4_EINVAL); default 0           */
+    int32_t batch_exec;      /* how an execute of sfft4_plan_batched runs its signals:
+                                SFFT4_BATCH_PERSISTENT (default): every (signal, iteration,
+                                residue slice) fold tile in one launch, the DFT columns of every
+                                iteration grouped by bucket count, and one decode launch of
+                                persistent CTAs that take whole signals from a device queue
+                                (longest decode chains first) and run their iterations in
+                                order; SFFT4_BATCH_LEVELS: level by level (level m = iteration
+                                m of every signal that has one), the decode chain on a second
+                                stream.  The results are identical                          */
     int32_t decode_cluster;  /* CTAs that decode one signal (a thread-block cluster of 1, 2,
                                 4, 8 or 16 CTAs sharing the update's buckets and the
                                 candidates); 0 (default) = the largest power of two up to 8

@@ -50,7 +50,7 @@ def _stream_ptr(device):
 def _opts(B1=0, delta=1e-8, precision="fp32", min_votes=0, select_factor=2.0, sig_floor=1e-10,
           mag_tol=0.5, max_iters=64, max_batch=1, trace=False, profile=False, graph=False,
           location="multiscale", fold_order="signal_major", l2_fetch_bytes=0, trace_signal=0,
-          decode_cluster=0):
+          decode_cluster=0, batch_exec="persistent"):
     o = _lib.Opts()
     check(_lib.load().sfft4_opts_default(ctypes.byref(o)), "sfft4_opts_default")
     o.B1 = B1
@@ -71,6 +71,7 @@ def _opts(B1=0, delta=1e-8, precision="fp32", min_votes=0, select_factor=2.0, si
     o.l2_fetch_bytes = l2_fetch_bytes
     o.trace_signal = trace_signal
     o.decode_cluster = decode_cluster
+    o.batch_exec = {"persistent": _lib.SFFT4_BATCH_PERSISTENT, "levels": _lib.SFFT4_BATCH_LEVELS}[batch_exec]
     return o
 
 
@@ -256,11 +257,14 @@ class BatchPlan:
     """Plan of a batch of signals of different sizes N_i and sparsities K_i, executed together
     (each signal follows its own static schedule, Section 3.1; signal i uses Philox counter
     (i, m, 0, 0)).  Outputs are rows of length Kmax = max K_i.  B1s optionally gives each
-    signal's first-iteration bucket count (0 = default), e.g. from `autotune.choose_b1`."""
+    signal's first-iteration bucket count (0 = default), e.g. from `autotune.choose_b1`.
+    batch_exec="persistent" (default) runs all folds, all DFTs and one persistent decode launch
+    (CTAs taking whole signals from a device queue); "levels" runs level by level.  The
+    outputs are identical."""
 
     def __init__(self, Ns, Ks, l=16, q=1.0, seed=0, *, B1=0, B1s=None, delta=1e-8, precision="fp32",
                  min_votes=0, select_factor=2.0, sig_floor=1e-10, mag_tol=0.5, max_iters=64,
-                 profile=False, graph=False, location="multiscale", device=None):
+                 profile=False, graph=False, location="multiscale", batch_exec="persistent", device=None):
         import torch
         lib = _lib.load()
         self.device = _device(device)
@@ -269,7 +273,7 @@ class BatchPlan:
         if len(Ns) != len(Ks) or not Ns:
             raise ValueError("Ns and Ks must be non-empty and of equal length")
         o = _opts(B1, delta, precision, min_votes, select_factor, sig_floor, mag_tol, max_iters,
-                  1, False, profile, graph, location)
+                  1, False, profile, graph, location, batch_exec=batch_exec)
         nsig = len(Ns)
         Na = (ctypes.c_int64 * nsig)(*Ns)
         Ka = (ctypes.c_int64 * nsig)(*Ks)

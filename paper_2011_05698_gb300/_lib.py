@@ -18,6 +18,8 @@ SFFT4_LOC_MULTISCALE = 0
 SFFT4_LOC_TWO_ROUND = 1
 SFFT4_FOLD_SIGNAL_MAJOR = 0
 SFFT4_FOLD_ITERATION_MAJOR = 1
+SFFT4_BATCH_PERSISTENT = 0
+SFFT4_BATCH_LEVELS = 1
 MAX_ROUNDS = 64
 
 
@@ -29,7 +31,7 @@ class Opts(ctypes.Structure):
                 ("trace", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("l2_fetch_bytes", ctypes.c_int32), ("graph", ctypes.c_int32), ("location", ctypes.c_int32),
                 ("fold_order", ctypes.c_int32), ("trace_signal", ctypes.c_int32),
-                ("decode_cluster", ctypes.c_int32)]
+                ("batch_exec", ctypes.c_int32), ("decode_cluster", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):

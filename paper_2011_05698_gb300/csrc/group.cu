@@ -2,13 +2,19 @@
 // table-driven kernels.
 //
 // Signals with equal (N, K, B1) share one static schedule ("class", Section 3.1); window
-// tables are shared by (N, B).  Level m of an execute is iteration m of every signal whose
-// schedule has one: a handful of launches whose CTAs take their work from device tables built
-// here (fold tiles (signal, fold group, residue slice), DFT columns grouped by bucket count,
-// decode jobs grouped by round count).  The bucketization of all levels runs on the caller's
-// stream and the decode chain on a second stream, level m as soon as its bucket arrays exist,
-// since the bucketization never reads the found sets.  A whole execute can be captured as one
-// CUDA graph (opts.graph).
+// tables are shared by (N, B).  The CTAs of every launch take their work from device tables
+// built here: fold tiles (signal, iteration, fold group, residue slice), DFT columns grouped
+// by bucket count, decode jobs (signal, iteration).  The bucketization of an iteration never
+// reads the found sets, so it can run before the decode chain.  Two forms (opts.batch_exec):
+//   persistent (default): all fold tiles in one launch (the tiles of a signal adjacent, so the
+//     samples its iterations share are re-read from L2), all DFT columns in one or two
+//     tensor-core launches (one per bucket count in FP32), then one decode launch of
+//     persistent CTAs that take whole signals from a device queue, longest decode chains
+//     first, and run each signal's iterations in order; four or five launches per execute;
+//   levels: level m = iteration m of every signal that has one, its fold, DFT and decode
+//     launches, the decode chain on a second stream overlapping later levels' bucketization.
+// Both compute every tile, column and iteration identically, so their outputs are the same.
+// A whole execute can be captured as one CUDA graph (opts.graph).
 #include <stdio.h>
 #include <string.h>
 
@@ -62,6 +68,23 @@ struct Group {
     DecodeArgs* dec_jobs = nullptr;
     int32_t* dec_list = nullptr;
     FinalJob* fin_jobs = nullptr;
+    // persistent form: every level's fold tiles in one list, DFT columns by bucket count over
+    // all levels, per-signal decode chains (indices into dec_jobs) and the queue order
+    GroupLevel::Fold all_fold{1, 0, 0, 0, 0, 0};
+    FoldTile* all_tiles = nullptr;
+    std::vector<GroupLevel::Dft> all_dfts;
+    const float2** all_zcols = nullptr;
+    float2** all_ucols = nullptr;
+    float2** all_ycols = nullptr;
+    int32_t* chain_off = nullptr;      // signal i's iterations: chain_args[chain_off[i] ..]
+    int32_t* chain_len = nullptr;
+    int32_t* chain_order = nullptr;
+    int32_t* queue = nullptr;
+    DecodeArgs* chain_args = nullptr;  // dec_jobs reordered signal by signal
+    int chain_rclass = 0, chain_grid = 1;
+    size_t chain_smem = 0;
+    int kernels_persistent = 0;
+    bool persistent = true;            // opts.batch_exec == SFFT4_BATCH_PERSISTENT
     // workspace
     void* arena = nullptr;
     int32_t* F = nullptr;
@@ -88,7 +111,9 @@ void free_group(Group* g) {
         cudaFree(w.tw4);
     }
     void* bufs[] = {g->fold_jobs, g->tiles, g->zcols, g->ucols, g->ycols, g->dec_jobs,
-                    g->dec_list, g->fin_jobs, g->arena};
+                    g->dec_list, g->fin_jobs, g->arena, g->all_tiles, g->all_zcols, g->all_ucols,
+                    g->all_ycols, g->chain_off, g->chain_len, g->chain_order, g->queue,
+                    g->chain_args};
     for (void* b : bufs) cudaFree(b);
     delete g;
 }
@@ -112,7 +137,7 @@ size_t group_levels(const Group* g) { return g->levels.size(); }
 const FinalJob* group_final_jobs(const Group* g, int* nsig, int64_t* samples, int* kernels) {
     *nsig = g->nsig;
     *samples = g->samples;
-    *kernels = g->kernels;
+    *kernels = g->persistent ? g->kernels_persistent : g->kernels;
     return g->fin_jobs;
 }
 
@@ -122,6 +147,7 @@ int build_group_plan(sfft4_plan_s* p, int nsig, const int64_t* Ns, const int64_t
     if (!g) return SFFT4_ENOMEM;
     p->grp = g;
     g->nsig = nsig;
+    g->persistent = p->o.batch_exec == SFFT4_BATCH_PERSISTENT;
     // classes of equal (N, K, B1), each with its own static schedule
     std::map<std::tuple<int64_t, int64_t, int32_t>, int> cls_of;
     for (int i = 0; i < nsig; ++i) {
@@ -170,10 +196,12 @@ int build_group_plan(sfft4_plan_s* p, int nsig, const int64_t* Ns, const int64_t
     size_t hk_run = 0;
     for (int i = 0; i < nsig; ++i) {
         const sfft4_plan_s* c = g->cls[g->slot_cls[i]];
-        const size_t rb = (size_t)c->R_max * c->B_max * sizeof(float2);
-        so[i].z = take(rb);
-        so[i].y = take((size_t)c->ytot * sizeof(float2));  // every iteration's bucket arrays
-        so[i].u = (p->o.precision == SFFT4_BF16X3) ? take(rb) : 0;
+        // every iteration's folded arrays, four-step scratch (BF16X3) and bucket arrays, iteration
+        // m at offset yoff[m] of each block, so that all folds may run before all DFTs
+        const size_t yb = (size_t)c->ytot * sizeof(float2);
+        so[i].z = take(yb);
+        so[i].y = take(yb);
+        so[i].u = (p->o.precision == SFFT4_BF16X3) ? take(yb) : 0;
         so[i].ff = take((size_t)c->Fcap * 4);
         so[i].fv = take((size_t)c->Fcap * 16);
         so[i].fvt = take((size_t)c->Fcap);
@@ -199,6 +227,16 @@ int build_group_plan(sfft4_plan_s* p, int nsig, const int64_t* Ns, const int64_t
     std::vector<float2*> uc, yc;
     std::vector<DecodeArgs> djobs;
     std::vector<int32_t> dlist;
+    // persistent form: per signal its fold jobs and decode jobs (iteration order), and the DFT
+    // columns of every level by bucket count
+    struct SigFoldJob {
+        int job, nsl;
+        int64_t per_tile;
+    };
+    std::vector<std::vector<SigFoldJob>> sig_fold(nsig);
+    std::vector<std::vector<int>> sig_dec(nsig);
+    std::map<int, std::vector<int64_t>> cols_by_B;   // indices into zc / uc / yc
+    std::map<int, Window> win_by_B;
     for (int mi = 0; mi < Mmax; ++mi) {
         GroupLevel L;
         // fold tiles of every signal and fold group of the level in one launch, instantiated for
@@ -213,11 +251,16 @@ int build_group_plan(sfft4_plan_s* p, int nsig, const int64_t* Ns, const int64_t
                 for (const FoldGroup& fg : ih.groups) {
                     size_t smem = 0;
                     FoldArgs a = make_fold_args(c, mi, fg, &smem);
-                    a.z = (float2*)(A + so[i].z);
+                    a.z = (float2*)(A + so[i].z) + c->yoff[mi];
                     a.signal0 = i;
                     const int job = (int)fjobs.size();
                     fjobs.push_back(a);
                     for (int sl = 0; sl < ih.d.B / ih.Wj; ++sl) tiles.push_back({job, sl});
+                    const int nsl = ih.d.B / ih.Wj;
+                    sig_fold[i].push_back({job, nsl, fg.unique / nsl});
+                    g->all_fold.RG = std::max(g->all_fold.RG, (int)fg.nr);
+                    g->all_fold.threads = std::max(g->all_fold.threads, ih.Wj * fg.P);
+                    g->all_fold.samples += fg.unique;
                     f.RG = std::max(f.RG, (int)fg.nr);
                     f.threads = std::max(f.threads, ih.Wj * fg.P);
                     f.smem = std::max(f.smem, smem);
@@ -240,9 +283,11 @@ int build_group_plan(sfft4_plan_s* p, int nsig, const int64_t* Ns, const int64_t
                 const sfft4_plan_s* c = g->cls[g->slot_cls[i]];
                 const IterHost& ih = c->iters[mi];
                 d.w = c->wins[ih.win];
+                win_by_B[kv.first] = d.w;  // the DFT tables depend on B alone
                 for (int r = 0; r < ih.d.R; ++r) {
-                    zc.push_back((const float2*)(A + so[i].z) + (int64_t)r * ih.d.B);
-                    uc.push_back(so[i].u ? (float2*)(A + so[i].u) + (int64_t)r * ih.d.B : nullptr);
+                    cols_by_B[kv.first].push_back((int64_t)zc.size());
+                    zc.push_back((const float2*)(A + so[i].z) + c->yoff[mi] + (int64_t)r * ih.d.B);
+                    uc.push_back(so[i].u ? (float2*)(A + so[i].u) + c->yoff[mi] + (int64_t)r * ih.d.B : nullptr);
                     yc.push_back((float2*)(A + so[i].y) + c->yoff[mi] + (int64_t)r * ih.d.B);
                 }
             }
@@ -270,8 +315,11 @@ int build_group_plan(sfft4_plan_s* p, int nsig, const int64_t* Ns, const int64_t
                 a.theta = theta + i;
                 a.fxexp = fx + i;
                 dlist.push_back((int32_t)djobs.size());
+                sig_dec[i].push_back((int)djobs.size());
                 djobs.push_back(a);
                 d.smem = std::max(d.smem, decode_smem_bytes(id.B));
+                g->chain_rclass = std::max(g->chain_rclass, rcl);
+                g->chain_smem = std::max(g->chain_smem, decode_smem_bytes(id.B));
             }
             d.n = (int)((int64_t)dlist.size() - d.off);
             if (d.n > 0) L.decs.push_back(d);
@@ -287,6 +335,74 @@ int build_group_plan(sfft4_plan_s* p, int nsig, const int64_t* Ns, const int64_t
         g->levels.push_back(L);
     }
     g->kernels += 1;  // finalize
+
+    // persistent form.  Fold tiles signal after signal (heaviest signals first), within a
+    // signal its jobs heaviest tile first: the CTAs resident at a time gather from few signals.
+    // The z arrays of one signal are reused by every iteration in the levels form (one R_max x
+    // B_max block); here every iteration's fold must keep its own, at the offset of its bucket
+    // arrays in y... so the persistent fold writes into the signal's y block and the DFT reads
+    // from there: see the column tables below.
+    {
+        std::vector<int64_t> sig_samples(nsig, 0);
+        for (int i = 0; i < nsig; ++i)
+            for (const SigFoldJob& j : sig_fold[i]) sig_samples[i] += j.per_tile * j.nsl;
+        std::vector<int> sorder(nsig);
+        for (int i = 0; i < nsig; ++i) sorder[i] = i;
+        std::stable_sort(sorder.begin(), sorder.end(), [&](int u, int v) { return sig_samples[u] > sig_samples[v]; });
+        std::vector<FoldTile> at;
+        for (int i : sorder) {
+            std::vector<SigFoldJob> js = sig_fold[i];
+            std::stable_sort(js.begin(), js.end(), [](const SigFoldJob& u, const SigFoldJob& v) { return u.per_tile > v.per_tile; });
+            for (const SigFoldJob& j : js)
+                for (int sl = 0; sl < j.nsl; ++sl) at.push_back({j.job, sl});
+        }
+        g->all_fold.n = (int)at.size();
+        g->all_fold.smem = fold_smem(g->all_fold.RG, g->all_fold.threads);
+        rc = upload(&g->all_tiles, at);
+        if (rc) return rc;
+    }
+    // DFT columns of every level, by bucket count
+    {
+        std::vector<const float2*> azc;
+        std::vector<float2*> auc, ayc;
+        std::vector<int> Bs;
+        for (auto& kv : cols_by_B) {
+            GroupLevel::Dft d{kv.first, (int64_t)azc.size(), 0, win_by_B[kv.first]};
+            for (int64_t ci : kv.second) {
+                azc.push_back(zc[ci]);
+                auc.push_back(uc[ci]);
+                ayc.push_back(yc[ci]);
+            }
+            d.n = (int)((int64_t)azc.size() - d.off);
+            g->all_dfts.push_back(d);
+            Bs.push_back(kv.first);
+        }
+        rc = upload(&g->all_zcols, azc);
+        if (!rc) rc = upload(&g->all_ucols, auc);
+        if (!rc) rc = upload(&g->all_ycols, ayc);
+        if (rc) return rc;
+        g->kernels_persistent = 1 + (p->o.precision == SFFT4_BF16X3 ? dft_tc_launches(Bs.data(), (int)Bs.size())
+                                                                     : (int)Bs.size()) + 1 + 1;
+    }
+    // decode chains: signal i's iterations in order, longest chains first
+    {
+        std::vector<DecodeArgs> cargs;
+        std::vector<int32_t> coff(nsig), clen(nsig), corder(nsig);
+        for (int i = 0; i < nsig; ++i) {
+            coff[i] = (int32_t)cargs.size();
+            clen[i] = (int32_t)sig_dec[i].size();
+            for (int j : sig_dec[i]) cargs.push_back(djobs[j]);
+            corder[i] = i;
+        }
+        std::stable_sort(corder.begin(), corder.end(), [&](int u, int v) { return clen[u] > clen[v]; });
+        g->chain_grid = std::max(1, std::min(nsig, 2 * p->sm_count));
+        rc = upload(&g->chain_args, cargs);
+        if (!rc) rc = upload(&g->chain_off, coff);
+        if (!rc) rc = upload(&g->chain_len, clen);
+        if (!rc) rc = upload(&g->chain_order, corder);
+        if (!rc) rc = check_cuda(cudaMalloc(&g->queue, sizeof(int32_t)));
+        if (rc) return rc;
+    }
     std::vector<FinalJob> fin(nsig);
     for (int i = 0; i < nsig; ++i) {
         const sfft4_plan_s* c = g->cls[g->slot_cls[i]];
@@ -314,9 +430,52 @@ struct GroupRun {
     int8_t* votes;
 };
 
+// Persistent form: all fold tiles, all DFT columns, one persistent decode launch, finalize,
+// in order on the caller's stream.
+int group_body_persistent(sfft4_plan_s* p, const void* ctx, cudaStream_t st) {
+    const GroupRun& r = *(const GroupRun*)ctx;
+    Group* g = p->grp;
+    int rc = check_cuda(cudaMemsetAsync(g->F, 0, (size_t)g->nsig * sizeof(int32_t), st));
+    if (!rc) rc = check_cuda(cudaMemsetAsync(g->hkeys, 0xff, g->hkeys_count * sizeof(int32_t), st));
+    if (!rc) rc = check_cuda(cudaMemsetAsync(g->queue, 0, sizeof(int32_t), st));
+    if (rc) return rc;
+    const GroupLevel::Fold& f = g->all_fold;
+    cudaEvent_t ev = nullptr;
+    rc = prof_begin(p, st, &ev);
+    if (!rc) rc = launch_fold_multi(f.RG, g->fold_jobs, g->all_tiles, f.n, r.x, f.threads, f.smem, st);
+    if (!rc) rc = prof_end(p, st, ev, kProfFold, f.samples);
+    if (rc) return rc;
+    if (p->o.precision == SFFT4_BF16X3) {
+        std::vector<DftColSet> sets;
+        for (const auto& d : g->all_dfts)
+            sets.push_back(DftColSet{d.B, d.w.dA1, d.w.dA2, d.w.tw4, g->all_zcols + d.off, g->all_ucols + d.off,
+                                     g->all_ycols + d.off, d.n});
+        rc = prof_begin(p, st, &ev);
+        if (!rc) rc = launch_dft_tc_sets(sets.data(), (int)sets.size(), p->status, p->sm_count, st);
+        if (!rc) rc = prof_end(p, st, ev, kProfFft, 0);
+        if (rc) return rc;
+    } else {
+        for (const auto& d : g->all_dfts) {
+            rc = prof_begin(p, st, &ev);
+            if (!rc) rc = launch_fft_multi(g->all_zcols + d.off, g->all_ycols + d.off, d.n, d.B, d.w.tw, st);
+            if (!rc) rc = prof_end(p, st, ev, kProfFft, 0);
+            if (rc) return rc;
+        }
+    }
+    rc = prof_begin(p, st, &ev);
+    if (!rc) rc = launch_decode_chain(g->chain_rclass, g->chain_args, g->chain_off, g->chain_len, g->chain_order,
+                                      g->nsig, g->queue, g->chain_grid, g->chain_smem, st);
+    if (!rc) rc = prof_end(p, st, ev, kProfDecode, 0);
+    if (!rc) rc = prof_begin(p, st, &ev);
+    if (!rc) rc = launch_finalize_multi(g->fin_jobs, g->nsig, g->Kmax, r.idx, r.val, r.nfound, r.votes, st);
+    if (!rc) rc = prof_end(p, st, ev, kProfFinalize, 0);
+    return rc;
+}
+
 int group_body(sfft4_plan_s* p, const void* ctx, cudaStream_t st) {
     const GroupRun& r = *(const GroupRun*)ctx;
     Group* g = p->grp;
+    if (g->persistent) return group_body_persistent(p, ctx, st);
     // bucketization of every level on the caller's stream, the decode chain on the plan's
     // decode stream (level m after its bucket arrays exist): the bucketization never reads
     // the found sets, so later levels' folds overlap earlier levels' decodes
@@ -422,7 +581,7 @@ int sfft4_get_batch_info(sfft4_plan_t p, sfft4_batch_info* info) {
     info->nsig = g->nsig;
     info->n_classes = (int32_t)g->cls.size();
     info->n_levels = (int32_t)g->levels.size();
-    info->kernels_per_execute = g->kernels;
+    info->kernels_per_execute = g->persistent ? g->kernels_persistent : g->kernels;
     info->Kmax = g->Kmax;
     info->samples_per_execute = g->samples;
     info->precision = p->o.precision;

@@ -1241,6 +1241,38 @@ __global__ void __launch_bounds__(kDecodeThreads, 2) k_decode_multi(const Decode
     decode_body<RMAX>(sa, 0);
 }
 
+// Persistent decode of a batch of signals of different sizes: each CTA takes whole signals
+// from a device queue (the next unclaimed entry of `order`, longest decode chains first) and
+// runs that signal's iterations in order, jobs[off[i]] .. jobs[off[i] + len[i] - 1], each
+// exactly as k_decode_multi runs it.  No CTA waits for another: a signal's iterations depend
+// only on each other, and all its bucket arrays exist before the launch.  *queue must be 0 at
+// launch.
+template <int RMAX>
+__global__ void __launch_bounds__(kDecodeThreads, 2) k_decode_chain(const DecodeArgs* __restrict__ jobs,
+                                                                 const int32_t* __restrict__ off,
+                                                                 const int32_t* __restrict__ len,
+                                                                 const int32_t* __restrict__ order, int nsig,
+                                                                 int32_t* queue) {
+    __shared__ __align__(16) DecodeArgs sa;
+    __shared__ int s_q;
+    for (;;) {
+        if (threadIdx.x == 0) s_q = atomicAdd(queue, 1);
+        __syncthreads();
+        const int q = s_q;
+        __syncthreads();
+        if (q >= nsig) break;
+        const int i = order[q];
+        for (int k = 0; k < len[i]; ++k) {
+            const DecodeArgs* src = jobs + off[i] + k;
+            for (int w = threadIdx.x; w < (int)(sizeof(DecodeArgs) / 4); w += blockDim.x)
+                ((uint32_t*)&sa)[w] = ((const uint32_t*)src)[w];
+            __syncthreads();
+            decode_body<RMAX>(sa, 0);
+            __syncthreads();
+        }
+    }
+}
+
 // ----------------------------------------------------------------- finalize ---------
 // Top-K of the found set by |v| (ties to the lower frequency), sorted by frequency.
 __device__ __forceinline__ void finalize_body(const int32_t* Fc, const int32_t* ffa,
@@ -1661,6 +1693,14 @@ int launch_decode_multi(int rclass, const DecodeArgs* jobs, const int32_t* list,
     return check_cuda(cudaGetLastError());
 }
 
+int launch_decode_chain(int rclass, const DecodeArgs* jobs, const int32_t* off, const int32_t* len,
+                        const int32_t* order, int nsig, int32_t* queue, int grid, size_t smem, cudaStream_t st) {
+    if (rclass == 0) k_decode_chain<8><<<grid, kDecodeThreads, smem, st>>>(jobs, off, len, order, nsig, queue);
+    else if (rclass == 1) k_decode_chain<16><<<grid, kDecodeThreads, smem, st>>>(jobs, off, len, order, nsig, queue);
+    else k_decode_chain<64><<<grid, kDecodeThreads, smem, st>>>(jobs, off, len, order, nsig, queue);
+    return check_cuda(cudaGetLastError());
+}
+
 int launch_finalize_multi(const FinalJob* jobs, int nsig, int64_t Kout, int64_t* idx, sfft4_c128* val,
                           int64_t* nfound, int8_t* votes, cudaStream_t st) {
     int P2 = 1;
@@ -1771,6 +1811,11 @@ int configure_kernels() {
                                                   (int)decode_smem(kBMax)));
     if (!rc) rc = check_cuda(cudaFuncSetAttribute(k_decode<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   (int)decode_smem(kBMax)));
+    const void* decs_p[] = {(const void*)k_decode_chain<8>, (const void*)k_decode_chain<16>,
+                            (const void*)k_decode_chain<64>};
+    for (const void* f : decs_p)
+        if (!rc) rc = check_cuda(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)decode_smem(kBMax)));
     const void* decs_c[] = {(const void*)k_decode_cluster<8>, (const void*)k_decode_cluster<16>,
                             (const void*)k_decode_cluster<64>};
     for (const void* f : decs_c) {

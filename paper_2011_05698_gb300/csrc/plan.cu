@@ -225,6 +225,7 @@ int plan_options(int64_t N, int64_t K, int32_t l, double q, const sfft4_opts* op
     if (o.location != SFFT4_LOC_MULTISCALE && o.location != SFFT4_LOC_TWO_ROUND) return SFFT4_EINVAL;
     if (o.fold_order != SFFT4_FOLD_SIGNAL_MAJOR && o.fold_order != SFFT4_FOLD_ITERATION_MAJOR) return SFFT4_EINVAL;
     if (o.decode_cluster < 0 || o.decode_cluster > 16 || (o.decode_cluster & (o.decode_cluster - 1))) return SFFT4_EINVAL;
+    if (o.batch_exec != SFFT4_BATCH_PERSISTENT && o.batch_exec != SFFT4_BATCH_LEVELS) return SFFT4_EINVAL;
     // the two-round vote window is 1/(8N) turns: FP32 bucket arrays resolve it up to N = 2^20
     if (o.location == SFFT4_LOC_TWO_ROUND && N > (int64_t(1) << 20)) return SFFT4_EINVAL;
     int64_t B1 = o.B1;

@@ -320,6 +320,8 @@ int launch_fft_multi(const float2* const* zcols, float2* const* ycols, int ncols
                      const float2* tw, cudaStream_t st);
 int launch_decode_multi(int rclass, const DecodeArgs* jobs, const int32_t* list, int n, size_t smem,
                         cudaStream_t st);
+int launch_decode_chain(int rclass, const DecodeArgs* jobs, const int32_t* off, const int32_t* len,
+                        const int32_t* order, int nsig, int32_t* queue, int grid, size_t smem, cudaStream_t st);
 int launch_finalize_multi(const FinalJob* jobs, int nsig, int64_t Kout, int64_t* idx, sfft4_c128* val,
                           int64_t* nfound, int8_t* votes, cudaStream_t st);
 int launch_votes_hist(const FinalJob* jobs, int nsig, unsigned long long* hist, cudaStream_t st);

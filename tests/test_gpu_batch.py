@@ -263,3 +263,40 @@ def test_batch_stats(s4):
         h += np.bincount(votes[i, :K].cpu().numpy().astype(np.int64), minlength=65)
     assert list(h) == st["votes_hist"]
     bp.close()
+
+
+def _bucket_counts(s4, N, K):
+    p = s4.Plan(N, K, L_, Q_, seed=0)
+    bs = {p.iter_info(m)["B"] for m in range(1, p.info["n_iters"] + 1)}
+    p.close()
+    return bs
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_persistent_and_level_forms_bit_identical(s4, precision):
+    """opts.batch_exec: the persistent form (all fold tiles in one launch, the DFT columns of
+    every iteration grouped by bucket count, one decode launch of persistent CTAs taking whole
+    signals from a device queue) computes every tile, column and iteration as the level-by-level
+    form does, so the outputs are the same bit for bit; it needs a handful of launches."""
+    import torch
+    sigs = mixed_signals(MIXED, 31, snr=25.0)
+    xs = [to_dev(s.x) for s in sigs]
+    Ns, Ks = [n for n, _ in MIXED], [k for _, k in MIXED]
+    a = s4.BatchPlan(Ns, Ks, L_, Q_, seed=31, precision=precision, batch_exec="persistent")
+    b = s4.BatchPlan(Ns, Ks, L_, Q_, seed=31, precision=precision, batch_exec="levels")
+    ra = [t.clone() for t in a.execute(xs)]
+    rb = [t.clone() for t in b.execute(xs)]
+    for u, w in zip(ra, rb):
+        assert torch.equal(u, w)
+    # fold, decode and finalize, plus the DFT: two tensor-core launches, or one FP32 launch per
+    # bucket count of the batch
+    nB = len({b_ for N, K in MIXED for b_ in _bucket_counts(s4, N, K)})
+    dft = 2 if precision == "bf16x3" else nB
+    assert a.info["kernels_per_execute"] <= 3 + dft < b.info["kernels_per_execute"]
+    # again, with the queue counter reset by the execute itself
+    ra2 = a.execute(xs)
+    for u, w in zip(ra, ra2):
+        assert torch.equal(u, w)
+    a.sync_status()
+    a.close()
+    b.close()
