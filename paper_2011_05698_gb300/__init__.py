@@ -86,19 +86,21 @@ class Plan:
     """A static sFFT4.0 plan (Section 3.1) for one (N, K, l, q, seed).  location="two_round"
     replaces the multiscale location by the two-round (tau = 0, 1) location of sFFT3.0 for
     exactly sparse signals.  fold_order="iteration_major" folds the batch one iteration at a
-    time instead of all iterations of a signal together (same results, more DRAM reads)."""
+    time instead of all iterations of a signal together (same results, more DRAM reads).
+    batch_exec="levels" decodes a batch iteration by iteration instead of in one persistent
+    launch (same results)."""
 
     def __init__(self, N, K, l=16, q=1.0, seed=0, *, B1=0, delta=1e-8, precision="fp32",
                  min_votes=0, select_factor=2.0, sig_floor=1e-10, mag_tol=0.5, max_iters=64,
                  max_batch=1, trace=False, profile=False, graph=False, location="multiscale",
                  fold_order="signal_major", l2_fetch_bytes=0, trace_signal=0, decode_cluster=0,
-                 device=None):
+                 batch_exec="persistent", device=None):
         import torch
         lib = _lib.load()
         self.device = _device(device)
         o = _opts(B1, delta, precision, min_votes, select_factor, sig_floor, mag_tol, max_iters,
                   max_batch, trace, profile, graph, location, fold_order, l2_fetch_bytes, trace_signal,
-                  decode_cluster)
+                  decode_cluster, batch_exec)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             check(lib.sfft4_plan(ctypes.byref(h), N, K, l, q, seed, ctypes.byref(o)), "sfft4_plan")

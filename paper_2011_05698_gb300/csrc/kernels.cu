@@ -1273,6 +1273,31 @@ __global__ void __launch_bounds__(kDecodeThreads, 2) k_decode_chain(const Decode
     }
 }
 
+// Persistent decode of a uniform batch: each CTA takes signals from a device queue and runs
+// iterations 1..M of that signal in order, iteration m exactly as k_decode runs it for the
+// signal.  All bucket arrays exist before the launch; no CTA waits for another.  *queue must be
+// 0 at launch.
+template <int RMAX>
+__global__ void __launch_bounds__(kDecodeThreads, 2) k_decode_chain_uniform(const DecodeArgs* __restrict__ iters,
+                                                                         int M, int nsig, int32_t* queue) {
+    __shared__ __align__(16) DecodeArgs sa;
+    __shared__ int s_q;
+    for (;;) {
+        if (threadIdx.x == 0) s_q = atomicAdd(queue, 1);
+        __syncthreads();
+        const int sig = s_q;
+        __syncthreads();
+        if (sig >= nsig) break;
+        for (int mi = 0; mi < M; ++mi) {
+            for (int w = threadIdx.x; w < (int)(sizeof(DecodeArgs) / 4); w += blockDim.x)
+                ((uint32_t*)&sa)[w] = ((const uint32_t*)(iters + mi))[w];
+            __syncthreads();
+            decode_body<RMAX>(sa, sig);
+            __syncthreads();
+        }
+    }
+}
+
 // ----------------------------------------------------------------- finalize ---------
 // Top-K of the found set by |v| (ties to the lower frequency), sorted by frequency.
 __device__ __forceinline__ void finalize_body(const int32_t* Fc, const int32_t* ffa,
@@ -1693,6 +1718,48 @@ int launch_decode_multi(int rclass, const DecodeArgs* jobs, const int32_t* list,
     return check_cuda(cudaGetLastError());
 }
 
+int build_decode_chain(sfft4_plan_s* p) {
+    std::vector<DecodeArgs> v;
+    p->dec_rclass = 0;
+    p->dec_smem = 0;
+    for (size_t mi = 0; mi < p->iters.size(); ++mi) {
+        v.push_back(make_decode_args(p, (int)mi));
+        const IterDev& d = p->iters[mi].d;
+        p->dec_rclass = std::max(p->dec_rclass, d.R <= 8 ? 0 : (d.R <= 16 ? 1 : 2));
+        p->dec_smem = std::max(p->dec_smem, decode_smem(d.B));
+    }
+    int rc = check_cuda(cudaMalloc(&p->dec_iters, v.size() * sizeof(DecodeArgs)));
+    if (!rc) rc = check_cuda(cudaMemcpy(p->dec_iters, v.data(), v.size() * sizeof(DecodeArgs), cudaMemcpyHostToDevice));
+    if (!rc) rc = check_cuda(cudaMalloc(&p->queue, sizeof(int32_t)));
+    return rc;
+}
+
+// Synchronous executes only: in a pipeline of asynchronous executes a persistent decode would
+// hold its CTA slots for the whole chain while the next batch's fold needs them (measured at
+// 256 signals of N = 2^22, K = 1000: 59 K against 85 K transforms/s), whereas the decodes of
+// single iterations interleave with the fold.
+bool decode_chain_used(const sfft4_plan_s* p, int nsig) {
+    return p->o.batch_exec == SFFT4_BATCH_PERSISTENT && !p->sm_fold.empty() && !p->o.trace && p->dec_iters &&
+           !p->in_async && decode_cluster_size(p, nsig) == 1;
+}
+
+int launch_decode_chain_uniform(sfft4_plan_s* p, int nsig, cudaStream_t st) {
+    int rc = configure_kernels();
+    if (!rc) rc = check_cuda(cudaMemsetAsync(p->queue, 0, sizeof(int32_t), st));
+    if (rc) return rc;
+    cudaEvent_t ev = nullptr;
+    rc = prof_begin(p, st, &ev);
+    if (rc) return rc;
+    const int grid = std::max(1, std::min(nsig, 2 * p->sm_count));
+    const int M = (int)p->iters.size();
+    if (p->dec_rclass == 0) k_decode_chain_uniform<8><<<grid, kDecodeThreads, p->dec_smem, st>>>(p->dec_iters, M, nsig, p->queue);
+    else if (p->dec_rclass == 1) k_decode_chain_uniform<16><<<grid, kDecodeThreads, p->dec_smem, st>>>(p->dec_iters, M, nsig, p->queue);
+    else k_decode_chain_uniform<64><<<grid, kDecodeThreads, p->dec_smem, st>>>(p->dec_iters, M, nsig, p->queue);
+    rc = check_cuda(cudaGetLastError());
+    if (rc) return rc;
+    return prof_end(p, st, ev, kProfDecode, 0);
+}
+
 int launch_decode_chain(int rclass, const DecodeArgs* jobs, const int32_t* off, const int32_t* len,
                         const int32_t* order, int nsig, int32_t* queue, int grid, size_t smem, cudaStream_t st) {
     if (rclass == 0) k_decode_chain<8><<<grid, kDecodeThreads, smem, st>>>(jobs, off, len, order, nsig, queue);
@@ -1812,7 +1879,8 @@ int configure_kernels() {
     if (!rc) rc = check_cuda(cudaFuncSetAttribute(k_decode<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   (int)decode_smem(kBMax)));
     const void* decs_p[] = {(const void*)k_decode_chain<8>, (const void*)k_decode_chain<16>,
-                            (const void*)k_decode_chain<64>};
+                            (const void*)k_decode_chain<64>, (const void*)k_decode_chain_uniform<8>,
+                            (const void*)k_decode_chain_uniform<16>, (const void*)k_decode_chain_uniform<64>};
     for (const void* f : decs_p)
         if (!rc) rc = check_cuda(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                       (int)decode_smem(kBMax)));
@@ -1976,15 +2044,18 @@ int run_body(sfft4_plan_s* p, const void* ctx, cudaStream_t st) {
         if (!rc) rc = check_cuda(cudaStreamWaitEvent(ds, p->ev[1], 0));
         if (rc) return rc;
     }
+    // persistent decode: every iteration's bucket arrays first, then one decode launch
+    const bool chain = decode_chain_used(p, nsig);
     for (size_t mi = 0; mi < ni; ++mi) {
         float2* ym = p->y + p->yoff[mi];
         if (!all_dft) {
             rc = sig_major ? launch_iter_dft(p, (int)mi, nsig, p->zall + p->yoff[mi], p->ytot, ym, p->ytot, st)
                            : launch_bucketize(p, (int)mi, nsig, x, x_stride, 0, ym, p->ytot, st);
-            if (!rc) rc = check_cuda(cudaEventRecord(p->ev[1 + mi], st));
-            if (!rc) rc = check_cuda(cudaStreamWaitEvent(ds, p->ev[1 + mi], 0));
+            if (!rc && !chain) rc = check_cuda(cudaEventRecord(p->ev[1 + mi], st));
+            if (!rc && !chain) rc = check_cuda(cudaStreamWaitEvent(ds, p->ev[1 + mi], 0));
             if (rc) return rc;
         }
+        if (chain) continue;
         const IterDev& d = p->iters[mi].d;
         const int64_t ts = p->o.trace_signal;  // the traced signal's workspace blocks
         if (p->o.trace) {
@@ -2005,6 +2076,14 @@ int run_body(sfft4_plan_s* p, const void* ctx, cudaStream_t st) {
             if (rc) return rc;
         }
     }
+    if (chain) {
+        if (!all_dft) {
+            rc = check_cuda(cudaEventRecord(p->ev[1], st));
+            if (!rc) rc = check_cuda(cudaStreamWaitEvent(ds, p->ev[1], 0));
+        }
+        if (!rc) rc = launch_decode_chain_uniform(p, nsig, ds);
+        if (rc) return rc;
+    }
     rc = launch_finalize(p, nsig, r.idx, r.val, r.nfound, r.votes, ds);
     if (!rc) rc = check_cuda(cudaEventRecord(p->ev[1 + ni], ds));
     if (!rc) rc = check_cuda(cudaStreamWaitEvent(st, p->ev[1 + ni], 0));
@@ -2016,7 +2095,7 @@ int run(sfft4_plan_s* p, int nsig, const float2* x, int64_t x_stride, int64_t* i
     if (p->grp) return SFFT4_ESTATE;
     if (p->o.trace && p->o.trace_signal >= nsig) return SFFT4_EINVAL;
     const RunArgs r{nsig, x, x_stride, idx, val, nfound, votes};
-    const uint64_t key[8] = {1, (uint64_t)nsig, (uint64_t)(uintptr_t)x, (uint64_t)x_stride,
+    const uint64_t key[8] = {p->in_async ? 3u : 1u, (uint64_t)nsig, (uint64_t)(uintptr_t)x, (uint64_t)x_stride,
                              (uint64_t)(uintptr_t)idx, (uint64_t)(uintptr_t)val,
                              (uint64_t)(uintptr_t)nfound, (uint64_t)(uintptr_t)votes};
     int rc = graph_run(p, key, st, run_body, &r);
@@ -2051,7 +2130,11 @@ int sfft4_execute_batched_async(sfft4_plan_t p, int32_t nsig, const void* x_dev,
     sfft4_plan_s* w = nullptr;
     cudaStream_t as = nullptr;
     int rc = async_begin(p, (cudaStream_t)stream, &w, &as);
-    if (!rc) rc = run(w, nsig, (const float2*)x_dev, x_stride, idx_dev, val_dev, nfound_dev, votes_dev, as);
+    if (!rc) {
+        w->in_async = true;
+        rc = run(w, nsig, (const float2*)x_dev, x_stride, idx_dev, val_dev, nfound_dev, votes_dev, as);
+        w->in_async = false;
+    }
     if (!rc) rc = async_end(p, as);
     return rc;
 }
@@ -2113,7 +2196,7 @@ int sfft4_stats(sfft4_plan_t p, sfft4_run_stats* out) {
     } else {
         out->samples_per_execute = p->samples * p->last_nsig;
         out->iterations = (int32_t)p->iters.size();
-        out->kernels_per_execute = uniform_kernels(p);
+        out->kernels_per_execute = uniform_kernels(p, p->last_nsig > 0 ? p->last_nsig : p->o.max_batch);
         for (int s = 0; s < p->last_nsig; ++s)
             jobs.push_back(FinalJob{p->F + s, p->ff + (int64_t)s * p->Fcap, p->fv + (int64_t)s * p->Fcap,
                                     p->fvotes + (int64_t)s * p->Fcap, p->Fcap, p->K});

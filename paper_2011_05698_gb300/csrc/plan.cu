@@ -99,7 +99,7 @@ void free_plan(sfft4_plan_s* p) {
             cudaFree(w.tw4);
         }
     }
-    void* bufs[] = {p->iters_dev, p->z, p->zall, p->uall, p->y, p->u, p->status, p->F, p->ff, p->fv, p->fvotes, p->hkeys,
+    void* bufs[] = {p->dec_iters, p->queue, p->iters_dev, p->z, p->zall, p->uall, p->y, p->u, p->status, p->F, p->ff, p->fv, p->fvotes, p->hkeys,
                     p->hvals, p->theta, p->fxexp, p->trace_y, p->trace_F, p->trace_ff,
                     p->trace_fv, p->trace_votes};
     for (void* b : bufs) cudaFree(b);
@@ -183,14 +183,15 @@ namespace sfft4 {
 
 // Kernel launches of one execute of a uniform plan: per iteration its fold groups, one FP32 DFT
 // or one/two tensor-core DFT stages, one decode; one finalize.
-int32_t uniform_kernels(const sfft4_plan_s* p) {
+int32_t uniform_kernels(const sfft4_plan_s* p, int nsig) {
     const bool sig_major = p->o.fold_order == SFFT4_FOLD_SIGNAL_MAJOR;
-    // finalize, and the fold launches covering every iteration (signal-major)
-    int32_t k = 1 + (sig_major ? std::max<int32_t>(1, (int32_t)p->sm_fold.size()) : 0);
+    const bool chain = decode_chain_used(p, nsig);
+    // finalize, the fold launches covering every iteration (signal-major), the persistent decode
+    int32_t k = 1 + (sig_major ? std::max<int32_t>(1, (int32_t)p->sm_fold.size()) : 0) + (chain ? 1 : 0);
     const bool tc = p->o.precision == SFFT4_BF16X3;
     int nsingle = 0, nfour = 0;  // BF16X3 DFT groups by stage count
     for (auto& ih : p->iters) {
-        k += (sig_major ? 0 : (int32_t)ih.groups.size()) + 1;  // folds, decode
+        k += (sig_major ? 0 : (int32_t)ih.groups.size()) + (chain ? 0 : 1);  // folds, decode
         if (!(sig_major && tc)) k += (tc && ih.d.B > 64) ? 2 : 1;
         (ih.d.B > 64 ? nfour : nsingle)++;
     }
@@ -472,6 +473,10 @@ int sfft4_plan(sfft4_plan_t* out, int64_t N, int64_t K, int32_t l, double q, uin
     CK(cudaMalloc(&p->hvals, mb * ((size_t)1 << p->Hlog) * sizeof(int32_t)));
     CK(cudaMalloc(&p->theta, mb * sizeof(float)));
     CK(cudaMalloc(&p->fxexp, mb * sizeof(int32_t)));
+    if (o.fold_order == SFFT4_FOLD_SIGNAL_MAJOR && !o.trace) {
+        const int rcd = sfft4::build_decode_chain(p);
+        if (rcd) { free_plan(p); return rcd; }
+    }
     if (o.trace) {
         CK(cudaMalloc(&p->trace_y, ni * rb * sizeof(float2)));
         CK(cudaMalloc(&p->trace_F, ni * sizeof(int32_t)));
@@ -548,7 +553,7 @@ int sfft4_get_plan_info(sfft4_plan_t p, sfft4_plan_info* info) {
     info->precision = p->o.precision;
     info->samples_per_transform = p->samples;
     info->found_capacity = p->Fcap;
-    info->kernels_per_execute = uniform_kernels(p);
+    info->kernels_per_execute = uniform_kernels(p, p->o.max_batch);
     return SFFT4_OK;
 }
 

@@ -257,6 +257,13 @@ struct sfft4_plan_s {
     bool sync_pending = false;
     int32_t* status = nullptr;  // 1 when a bounded device wait gave up
     int sm_count = 0;
+    // persistent decode of a signal-major batch (opts.batch_exec): every iteration's decode
+    // arguments, the queue counter of the launch, its round class and shared memory
+    sfft4::DecodeArgs* dec_iters = nullptr;
+    bool in_async = false;      // set while an asynchronous execute runs on this workspace
+    int32_t* queue = nullptr;
+    int32_t dec_rclass = 0;
+    size_t dec_smem = 0;
     float* theta = nullptr;     // [sig] candidate floor
     int32_t* fxexp = nullptr;   // [sig] fixed-point exponent of the bucket update
     // trace of signal 0 (opts.trace)
@@ -297,6 +304,11 @@ int build_window_tables(sfft4_plan_s* p, Window* w, double delta);
 int launch_bucketize(sfft4_plan_s* p, int m_index, int nsig, const float2* x, int64_t x_stride,
                      int32_t signal0, float2* y_out, int64_t y_sig_stride, cudaStream_t st);
 int launch_decode(sfft4_plan_s* p, int m_index, int nsig, cudaStream_t st);
+// Whether an execute of nsig signals decodes in one persistent launch (opts.batch_exec
+// persistent, signal-major fold, one CTA per signal, no trace), and that launch.
+bool decode_chain_used(const sfft4_plan_s* p, int nsig);
+int launch_decode_chain_uniform(sfft4_plan_s* p, int nsig, cudaStream_t st);
+int build_decode_chain(sfft4_plan_s* p);
 int launch_finalize(sfft4_plan_s* p, int nsig, int64_t* idx, sfft4_c128* val, int64_t* nfound,
                     int8_t* votes, cudaStream_t st);
 int launch_reset(sfft4_plan_s* p, int nsig, cudaStream_t st);
@@ -348,7 +360,7 @@ int64_t window_halfwidth(int64_t B, double delta, double* s_t_out);
 int plan_options(int64_t N, int64_t K, int32_t l, double q, const sfft4_opts* opts, sfft4_opts* out,
                  int* qn_out);
 int plan_schedule(sfft4_plan_s* p);
-int32_t uniform_kernels(const sfft4_plan_s* p);
+int32_t uniform_kernels(const sfft4_plan_s* p, int nsig);
 int plan_tables(sfft4_plan_s* p, std::vector<Window>* cache);
 // Implemented in dft_tc.cu.
 size_t dft_tc_matrix_bytes();
