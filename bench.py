@@ -276,20 +276,21 @@ def uneven_form(s4, args, dev, stream, dist):
     xs = [device_signal(int(Ns[i]), int(Ks[i]), signal_seed(seed, i), snrs[i], dev)[0] for i in range(nsig)]
     graph = not args.no_graph
     B1s, tune = None, None
+    f_res = f_rnd = 0
     if not args.no_autotune:
         import collections
         import tempfile
         from paper_2011_05698_gb300 import autotune
         cache = os.path.join(tempfile.gettempdir(), "sfft4_autotune_bench.json")
-        B1s = autotune.choose_b1(Ns.tolist(), Ks.tolist(), L_DEF, Q_DEF, precision=args.precision,
-                                 cache_path=cache, device=dev)
+        B1s, f_res, f_rnd = autotune.choose(Ns.tolist(), Ks.tolist(), L_DEF, Q_DEF, precision=args.precision,
+                                            cache_path=cache, device=dev)
         ratio = collections.Counter()
         for b, k in zip(B1s, Ks.tolist()):
             ratio[f"{b / autotune._pow2ceil(2 * k):g}" if b else "default"] += 1
-        tune = {"seconds": autotune.choose_b1.last_seconds, "cache": cache,
-                "B1_over_pow2ceil_2K": dict(ratio)}
+        tune = {"seconds": autotune.choose.last_seconds, "cache": cache,
+                "B1_over_pow2ceil_2K": dict(ratio), "fold_residues": f_res, "fold_rounds": f_rnd}
     bp = s4.BatchPlan(Ns.tolist(), Ks.tolist(), L_DEF, Q_DEF, seed=seed, precision=args.precision, graph=graph,
-                      B1s=B1s)
+                      B1s=B1s, fold_residues=f_res, fold_rounds=f_rnd)
     out = bp.outputs()
     outs = [out, bp.outputs(), bp.outputs()]  # one per batch in flight
     ptrs = bp.pointers(xs)
@@ -319,7 +320,8 @@ def uneven_form(s4, args, dev, stream, dist):
     # the same launches issued directly (no graph), for comparison
     direct = None
     if graph:
-        bd = s4.BatchPlan(Ns.tolist(), Ks.tolist(), L_DEF, Q_DEF, seed=seed, precision=args.precision, B1s=B1s)
+        bd = s4.BatchPlan(Ns.tolist(), Ks.tolist(), L_DEF, Q_DEF, seed=seed, precision=args.precision, B1s=B1s,
+                          fold_residues=f_res, fold_rounds=f_rnd)
         outd = bd.outputs()
         ptrd = bd.pointers(xs)
         ed = max_over_ranks(timed(lambda: bd.execute(xs, out=outd, ptrs=ptrd), steps, args.warmup, stream, dist),
@@ -327,7 +329,7 @@ def uneven_form(s4, args, dev, stream, dist):
         direct = {"value": nsig * steps * world / ed, "ms_per_step": 1e3 * ed / steps}
         bd.close()
     bq = s4.BatchPlan(Ns.tolist(), Ks.tolist(), L_DEF, Q_DEF, seed=seed, precision=args.precision, profile=True,
-                      B1s=B1s)
+                      B1s=B1s, fold_residues=f_res, fold_rounds=f_rnd)
     outq = bq.outputs()
     bq.execute(xs, out=outq)
     torch.cuda.synchronize()

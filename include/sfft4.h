@@ -121,6 +121,13 @@ typedef struct {
                                 order; SFFT4_BATCH_LEVELS: level by level (level m = iteration
                                 m of every signal that has one), the decode chain on a second
                                 stream.  The results are identical                          */
+    int32_t fold_residues;   /* fold tile shape: residues mod B per fold CTA (16, 32 or 64,
+                                at most B); default 32                                      */
+    int32_t fold_rounds;     /* fold tile shape: most rounds one fold CTA accumulates (1..8;
+                                an iteration's rounds are split into balanced groups of at
+                                most this many); default 6.  Both change the order of the
+                                fold's sums (results agree to FP32 rounding, not bit for
+                                bit); an autotuner may pick them per (N, K)                 */
     int32_t decode_cluster;  /* CTAs that decode one signal (a thread-block cluster of 1, 2,
                                 4, 8 or 16 CTAs sharing the update's buckets and the
                                 candidates); 0 (default) = the largest power of two up to 8

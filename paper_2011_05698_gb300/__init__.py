@@ -50,7 +50,7 @@ def _stream_ptr(device):
 def _opts(B1=0, delta=1e-8, precision="fp32", min_votes=0, select_factor=2.0, sig_floor=1e-10,
           mag_tol=0.5, max_iters=64, max_batch=1, trace=False, profile=False, graph=False,
           location="multiscale", fold_order="signal_major", l2_fetch_bytes=0, trace_signal=0,
-          decode_cluster=0, batch_exec="persistent"):
+          decode_cluster=0, batch_exec="persistent", fold_residues=0, fold_rounds=0):
     o = _lib.Opts()
     check(_lib.load().sfft4_opts_default(ctypes.byref(o)), "sfft4_opts_default")
     o.B1 = B1
@@ -72,6 +72,8 @@ def _opts(B1=0, delta=1e-8, precision="fp32", min_votes=0, select_factor=2.0, si
     o.trace_signal = trace_signal
     o.decode_cluster = decode_cluster
     o.batch_exec = {"persistent": _lib.SFFT4_BATCH_PERSISTENT, "levels": _lib.SFFT4_BATCH_LEVELS}[batch_exec]
+    o.fold_residues = fold_residues
+    o.fold_rounds = fold_rounds
     return o
 
 
@@ -94,13 +96,13 @@ class Plan:
                  min_votes=0, select_factor=2.0, sig_floor=1e-10, mag_tol=0.5, max_iters=64,
                  max_batch=1, trace=False, profile=False, graph=False, location="multiscale",
                  fold_order="signal_major", l2_fetch_bytes=0, trace_signal=0, decode_cluster=0,
-                 batch_exec="persistent", device=None):
+                 batch_exec="persistent", fold_residues=0, fold_rounds=0, device=None):
         import torch
         lib = _lib.load()
         self.device = _device(device)
         o = _opts(B1, delta, precision, min_votes, select_factor, sig_floor, mag_tol, max_iters,
                   max_batch, trace, profile, graph, location, fold_order, l2_fetch_bytes, trace_signal,
-                  decode_cluster, batch_exec)
+                  decode_cluster, batch_exec, fold_residues, fold_rounds)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             check(lib.sfft4_plan(ctypes.byref(h), N, K, l, q, seed, ctypes.byref(o)), "sfft4_plan")
@@ -266,7 +268,8 @@ class BatchPlan:
 
     def __init__(self, Ns, Ks, l=16, q=1.0, seed=0, *, B1=0, B1s=None, delta=1e-8, precision="fp32",
                  min_votes=0, select_factor=2.0, sig_floor=1e-10, mag_tol=0.5, max_iters=64,
-                 profile=False, graph=False, location="multiscale", batch_exec="persistent", device=None):
+                 profile=False, graph=False, location="multiscale", batch_exec="persistent", fold_residues=0,
+                 fold_rounds=0, device=None):
         import torch
         lib = _lib.load()
         self.device = _device(device)
@@ -275,7 +278,8 @@ class BatchPlan:
         if len(Ns) != len(Ks) or not Ns:
             raise ValueError("Ns and Ks must be non-empty and of equal length")
         o = _opts(B1, delta, precision, min_votes, select_factor, sig_floor, mag_tol, max_iters,
-                  1, False, profile, graph, location, batch_exec=batch_exec)
+                  1, False, profile, graph, location, batch_exec=batch_exec, fold_residues=fold_residues,
+                  fold_rounds=fold_rounds)
         nsig = len(Ns)
         Na = (ctypes.c_int64 * nsig)(*Ns)
         Ka = (ctypes.c_int64 * nsig)(*Ks)

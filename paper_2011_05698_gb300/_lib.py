@@ -31,7 +31,8 @@ class Opts(ctypes.Structure):
                 ("trace", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("l2_fetch_bytes", ctypes.c_int32), ("graph", ctypes.c_int32), ("location", ctypes.c_int32),
                 ("fold_order", ctypes.c_int32), ("trace_signal", ctypes.c_int32),
-                ("batch_exec", ctypes.c_int32), ("decode_cluster", ctypes.c_int32)]
+                ("batch_exec", ctypes.c_int32), ("fold_residues", ctypes.c_int32),
+                ("fold_rounds", ctypes.c_int32), ("decode_cluster", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):

@@ -1,4 +1,5 @@
-"""Autotuner of the first-iteration bucket count B1 per (N, K class).
+"""Autotuner of the plan per (N, K class): the first-iteration bucket count B1 and the fold's
+tile shape (residues per fold CTA, rounds per fold group).
 
 B1 sets the whole static schedule (Section 3.1): more buckets isolate more coefficients per
 iteration but widen the window (w ~ 44 B1 samples at delta = 1e-8) and the DFT; fewer buckets
@@ -8,11 +9,17 @@ each (N, pow2ceil(K)) class the tuner times the candidates pow2ceil(2K) x {1/4, 
 large enough to fill the GPU (about 2^27 signal samples per execute, so the time is throughput,
 not the latency of one schedule), keeps those that recover every probe's support exactly, and
 picks the fastest, keeping the default unless another candidate is at least 3 % faster.
-Choices are cached in a JSON file keyed by device, precision, N, K class, l and q.
+With B1 chosen, the fold's tile shape is tuned the same way, one knob after the other:
+residues per fold CTA in {16, 32, 64} (the window width w follows from B and delta, so B1 also
+sets w), then the most rounds one fold CTA accumulates in {4, 6, 8}; the defaults (32, 6) stay
+unless another value is at least 3 % faster.  The tile shape changes the order of the fold's
+sums, so outputs agree with the default's to FP32 rounding.  Choices are cached in a JSON file
+keyed by device, precision, N, K class, l and q.
 
     from paper_2011_05698_gb300 import autotune
-    B1s = autotune.choose_b1(Ns, Ks, l=16, q=1.0, precision="bf16x3")
-    plan = BatchPlan(Ns, Ks, 16, 1.0, seed, B1s=B1s, precision="bf16x3")
+    B1s, residues, rounds = autotune.choose(Ns, Ks, l=16, q=1.0, precision="bf16x3")
+    plan = BatchPlan(Ns, Ks, 16, 1.0, seed, B1s=B1s, precision="bf16x3",
+                     fold_residues=residues, fold_rounds=rounds)
 """
 
 import json
@@ -70,53 +77,100 @@ def saturating_batch(N):
     return int(min(512, max(8, (1 << 27) // N)))
 
 
-def tune_one(N, K, l=16, q=1.0, precision="bf16x3", device=None, batch=None, reps=3, seed=12345):
-    """Time every candidate B1 of (N, K) on `batch` probe signals (default: a saturating
-    batch); returns a record with the chosen B1 (0 when no candidate recovers every probe,
-    i.e. keep the default)."""
+RESIDUES = (16, 32, 64)      # residues mod B per fold CTA; default 32
+ROUNDS = (4, 6, 8)           # most rounds per fold group; default 6
+DEFAULT_SHAPE = (32, 6)
+
+
+def _time_plan(N, K, l, q, precision, xs, supports, seed, reps, **kw):
+    """(ms per transform, exact support on every probe, plan info) of one plan, or None when
+    the planner rejects the options."""
     import numpy as np
+    import torch
+    batch = xs.shape[0]
+    try:
+        p = Plan(N, K, l, q, seed=seed, max_batch=batch, precision=precision, device=xs.device, **kw)
+    except Sfft4Error:
+        return None
+    out = p._outputs(batch)
+    p.execute_batched(xs, out)
+    idx, nf = out[0].cpu().numpy(), out[2].cpu().numpy()
+    ok = all(np.array_equal(idx[i, :nf[i]], supports[i]) for i in range(batch))
+    stream = torch.cuda.current_stream(xs.device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        p.execute_batched(xs, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    info = dict(p.info)
+    p.close()
+    return e0.elapsed_time(e1) / reps / batch, ok, info
+
+
+def _pick(tried, is_default):
+    """The fastest exact candidate, unless the default is within 3 % of it."""
+    good = [t for t in tried if t["exact_support"]]
+    if not good:
+        return None
+    best = min(good, key=lambda t: t["ms_per_transform"])
+    default = next((t for t in good if is_default(t)), None)
+    if default is not None and best["ms_per_transform"] > 0.97 * default["ms_per_transform"]:
+        return default
+    return best
+
+
+def tune_one(N, K, l=16, q=1.0, precision="bf16x3", device=None, batch=None, reps=3, seed=12345, shape=True):
+    """Time every candidate B1 of (N, K) on `batch` probe signals (default: a saturating
+    batch), then (shape=True) the fold tile shapes with the chosen B1; returns a record with
+    the chosen B1 (0 when no candidate recovers every probe, i.e. keep the default) and the
+    chosen residues per fold CTA and rounds per fold group."""
     import torch
     if device is None:
         device = torch.device("cuda", torch.cuda.current_device())
     if batch is None:
         batch = saturating_batch(N)
     xs, supports = probe_signals(N, K, batch, seed, device)
-    stream = torch.cuda.current_stream(xs.device)
     tried = []
     for b in candidates(N, K):
-        try:
-            p = Plan(N, K, l, q, seed=seed, B1=b, max_batch=batch, precision=precision, device=xs.device)
-        except Sfft4Error:
+        r = _time_plan(N, K, l, q, precision, xs, supports, seed, reps, B1=b)
+        if r is None:
             continue
-        out = p._outputs(batch)
-        p.execute_batched(xs, out)
-        idx, nf = out[0].cpu().numpy(), out[2].cpu().numpy()
-        ok = all(np.array_equal(idx[i, :nf[i]], supports[i]) for i in range(batch))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(reps):
-            p.execute_batched(xs, out)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps / batch
+        ms, ok, info = r
         tried.append({"B1": b, "ms_per_transform": ms, "exact_support": ok,
-                      "samples": p.info["samples_per_transform"], "iterations": p.info["n_iters"]})
-        p.close()
-    good = [t for t in tried if t["exact_support"]]
-    best = min(good, key=lambda t: t["ms_per_transform"]) if good else None
-    default = next((t for t in good if t["B1"] == _pow2ceil(2 * K)), None)
-    if best is not None and default is not None and best["ms_per_transform"] > 0.97 * default["ms_per_transform"]:
-        best = default
-    return {"N": N, "K": K, "batch": batch, "B1": best["B1"] if best else 0, "tried": tried}
+                      "samples": info["samples_per_transform"], "iterations": info["n_iters"]})
+    best = _pick(tried, lambda t: t["B1"] == _pow2ceil(2 * K))
+    rec = {"N": N, "K": K, "batch": batch, "B1": best["B1"] if best else 0, "tried": tried,
+           "fold_residues": DEFAULT_SHAPE[0], "fold_rounds": DEFAULT_SHAPE[1], "tried_shape": []}
+    if not shape:
+        return rec
+    res, rnd = DEFAULT_SHAPE
+    for knob, values in (("fold_residues", RESIDUES), ("fold_rounds", ROUNDS)):
+        tr = []
+        for v in values:
+            kw = {"fold_residues": res, "fold_rounds": rnd}
+            kw[knob] = v
+            r = _time_plan(N, K, l, q, precision, xs, supports, seed, reps, B1=rec["B1"], **kw)
+            if r is None:
+                continue
+            tr.append({**kw, "ms_per_transform": r[0], "exact_support": r[1]})
+        pick = _pick(tr, lambda t: t[knob] == DEFAULT_SHAPE[0 if knob == "fold_residues" else 1])
+        if pick is not None:
+            res, rnd = pick["fold_residues"], pick["fold_rounds"]
+        rec["tried_shape"].extend(tr)
+    rec["fold_residues"], rec["fold_rounds"] = res, rnd
+    return rec
 
 
 def _key(dev_name, precision, N, Kc, l, q):
-    return f"{dev_name}|{precision}|N={N}|Kc={Kc}|l={l}|q={q}"
+    return f"v2|{dev_name}|{precision}|N={N}|Kc={Kc}|l={l}|q={q}"
 
 
-def choose_b1(Ns, Ks, l=16, q=1.0, precision="bf16x3", cache_path=None, device=None, batch=None, log=None):
-    """First-iteration bucket count for every signal (list aligned with Ns), tuning each
-    (N, pow2ceil(K)) class not yet in the cache with the class's largest K."""
+def _records(Ns, Ks, l, q, precision, cache_path, device, batch, log, shape_of_top=False):
+    """The cached (or newly tuned) record of every (N, pow2ceil(K)) class of the batch, tuning
+    the B1 of each class not yet in the cache with its largest K, and (shape_of_top) the fold
+    tile shape of the class carrying the most samples; returns (records by class, key of a
+    signal)."""
     import torch
     device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
     dev_name = torch.cuda.get_device_name(device)
@@ -129,13 +183,20 @@ def choose_b1(Ns, Ks, l=16, q=1.0, precision="bf16x3", cache_path=None, device=N
     for N, K in zip(Ns, Ks):
         kc = _pow2ceil(int(K))
         classes[(int(N), kc)] = max(classes.get((int(N), kc), 0), int(K))
+    weight = {}
+    for N, K in zip(Ns, Ks):
+        c = (int(N), _pow2ceil(int(K)))
+        weight[c] = weight.get(c, 0) + int(N)
+    top = max(weight, key=weight.get)
     t0 = time.time()
     changed = False
     for (N, kc), kmax in sorted(classes.items()):
         key = _key(dev_name, precision, N, kc, l, q)
-        if key in cache:
+        need_shape = shape_of_top and (N, kc) == top
+        if key in cache and (not need_shape or cache[key].get("shape_tuned")):
             continue
-        rec = tune_one(N, kmax, l, q, precision, device, batch=batch)
+        rec = tune_one(N, kmax, l, q, precision, device, batch=batch, shape=need_shape)
+        rec["shape_tuned"] = need_shape
         cache[key] = rec
         changed = True
         if log is not None:
@@ -146,5 +207,26 @@ def choose_b1(Ns, Ks, l=16, q=1.0, precision="bf16x3", cache_path=None, device=N
         with open(tmp, "w") as fh:
             json.dump(cache, fh, indent=1)
         os.replace(tmp, path)
-    choose_b1.last_seconds = time.time() - t0
-    return [cache[_key(dev_name, precision, int(N), _pow2ceil(int(K)), l, q)]["B1"] for N, K in zip(Ns, Ks)]
+    _records.last_seconds = time.time() - t0
+    return cache, lambda N, K: _key(dev_name, precision, int(N), _pow2ceil(int(K)), l, q)
+
+
+def choose_b1(Ns, Ks, l=16, q=1.0, precision="bf16x3", cache_path=None, device=None, batch=None, log=None):
+    """First-iteration bucket count for every signal (list aligned with Ns)."""
+    cache, key = _records(Ns, Ks, l, q, precision, cache_path, device, batch, log)
+    choose_b1.last_seconds = _records.last_seconds
+    return [cache[key(N, K)]["B1"] for N, K in zip(Ns, Ks)]
+
+
+def choose(Ns, Ks, l=16, q=1.0, precision="bf16x3", cache_path=None, device=None, batch=None, log=None):
+    """(B1 per signal, residues per fold CTA, rounds per fold group) for a batch: the fold's
+    tile shape is an option of the whole batch, so it is the shape tuned for the class that
+    carries the most samples (signals x N)."""
+    cache, key = _records(Ns, Ks, l, q, precision, cache_path, device, batch, log, shape_of_top=True)
+    choose.last_seconds = _records.last_seconds
+    weight = {}
+    for N, K in zip(Ns, Ks):
+        weight[key(N, K)] = weight.get(key(N, K), 0) + int(N)
+    top = cache[max(weight, key=weight.get)]
+    return ([cache[key(N, K)]["B1"] for N, K in zip(Ns, Ks)],
+            int(top.get("fold_residues", DEFAULT_SHAPE[0])), int(top.get("fold_rounds", DEFAULT_SHAPE[1])))

@@ -1737,10 +1737,15 @@ int build_decode_chain(sfft4_plan_s* p) {
 // Synchronous executes only: in a pipeline of asynchronous executes a persistent decode would
 // hold its CTA slots for the whole chain while the next batch's fold needs them (measured at
 // 256 signals of N = 2^22, K = 1000: 59 K against 85 K transforms/s), whereas the decodes of
-// single iterations interleave with the fold.
+// single iterations interleave with the fold.  BF16X3 only: there every iteration's DFT runs
+// in grouped launches before the first decode anyway, while the FP32 DFTs (one launch per
+// iteration) overlap the decodes of earlier iterations, which the persistent decode would give
+// up.  One CTA per signal only: a cluster running every iteration of one signal in one launch
+// measured no faster than one launch per iteration (the gaps between launches on a stream are
+// small next to the 30-40 us of each iteration's decode).
 bool decode_chain_used(const sfft4_plan_s* p, int nsig) {
-    return p->o.batch_exec == SFFT4_BATCH_PERSISTENT && !p->sm_fold.empty() && !p->o.trace && p->dec_iters &&
-           !p->in_async && decode_cluster_size(p, nsig) == 1;
+    return p->o.batch_exec == SFFT4_BATCH_PERSISTENT && !p->sm_fold.empty() && p->uall && !p->o.trace &&
+           p->dec_iters && !p->in_async && decode_cluster_size(p, nsig) == 1;
 }
 
 int launch_decode_chain_uniform(sfft4_plan_s* p, int nsig, cudaStream_t st) {

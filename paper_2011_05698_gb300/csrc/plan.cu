@@ -227,6 +227,9 @@ int plan_options(int64_t N, int64_t K, int32_t l, double q, const sfft4_opts* op
     if (o.fold_order != SFFT4_FOLD_SIGNAL_MAJOR && o.fold_order != SFFT4_FOLD_ITERATION_MAJOR) return SFFT4_EINVAL;
     if (o.decode_cluster < 0 || o.decode_cluster > 16 || (o.decode_cluster & (o.decode_cluster - 1))) return SFFT4_EINVAL;
     if (o.batch_exec != SFFT4_BATCH_PERSISTENT && o.batch_exec != SFFT4_BATCH_LEVELS) return SFFT4_EINVAL;
+    if (o.fold_residues != 0 && o.fold_residues != 16 && o.fold_residues != 32 && o.fold_residues != 64)
+        return SFFT4_EINVAL;
+    if (o.fold_rounds < 0 || o.fold_rounds > kFoldRG) return SFFT4_EINVAL;
     // the two-round vote window is 1/(8N) turns: FP32 bucket arrays resolve it up to N = 2^20
     if (o.location == SFFT4_LOC_TWO_ROUND && N > (int64_t(1) << 20)) return SFFT4_EINVAL;
     int64_t B1 = o.B1;
@@ -315,11 +318,12 @@ int plan_schedule(sfft4_plan_s* p) {
         // residues per fold CTA: 32 (measured against 16 and 64: small enough that the
         // CTAs resident at a time cover few signals in signal-major order; one warp's window
         // coefficient loads are then 32 contiguous floats)
-        ih.Wj = (int32_t)std::min<int64_t>(B, 32);
+        ih.Wj = (int32_t)std::min<int64_t>(B, p->o.fold_residues ? p->o.fold_residues : 32);
         ih.unique = 0;
         // balanced groups of at most kFoldGroupMax rounds (the fold kernel's accumulator count
         // is the largest group of its launch)
-        const int ngr = (d.R + kFoldGroupMax - 1) / kFoldGroupMax, gsz = (d.R + ngr - 1) / ngr;
+        const int gmax = p->o.fold_rounds ? p->o.fold_rounds : kFoldGroupMax;
+        const int ngr = (d.R + gmax - 1) / gmax, gsz = (d.R + ngr - 1) / ngr;
         for (int r0 = 0; r0 < d.R; r0 += gsz) {
             FoldGroup g;
             build_group(&g, d.tau, r0, std::min(gsz, d.R - r0), d.h);

@@ -60,3 +60,29 @@ def test_per_signal_b1_matches_uniform_plan(s4):
         assert np.array_equal(idx[i, :int(nf[i])].cpu().numpy(), sigs[i].freqs)
         p.close()
     bp.close()
+
+
+def test_tile_shape_tuning_and_oracle_parity(s4, tmp_path):
+    """The fold tile shape (residues per fold CTA, rounds per fold group): the tuner keeps the
+    fastest exact candidate (or the default within 3 %), and a plan with a non-default shape
+    still matches the oracle (its fold sums in another order: FP32-rounding differences)."""
+    from oracle import plan as OP, sfft4 as O
+    from paper_2011_05698_gb300 import autotune
+    rec = autotune.tune_one(2**16, 50, 16, 1.0, "bf16x3", batch=8)
+    assert rec["fold_residues"] in autotune.RESIDUES and rec["fold_rounds"] in autotune.ROUNDS
+    assert rec["tried_shape"] and all(t["exact_support"] for t in rec["tried_shape"])
+    B1s, res, rnd = autotune.choose([2**16, 2**14], [50, 16], 16, 1.0, "fp32", cache_path=str(tmp_path / "t.json"),
+                                    batch=4)
+    assert len(B1s) == 2 and res in autotune.RESIDUES and rnd in autotune.ROUNDS
+    import torch
+    N, K = 2**20, 100
+    sig = sparse_signal(N, K, 3, None)
+    for res, rnd in ((16, 4), (64, 8)):
+        p = s4.Plan(N, K, 4, 1.0, seed=3, fold_residues=res, fold_rounds=rnd)
+        idx, val, nf, _ = p.execute(torch.from_numpy(sig.x).to("cuda"))
+        n = int(nf)
+        r = O.run(sig.x.astype(np.complex128), OP.make_plan(N, K, 4, 1.0, seed=3))
+        assert np.array_equal(idx[:n].cpu().numpy(), r["f"]) and np.array_equal(r["f"], sig.freqs)
+        v = val[:n].cpu().numpy()
+        assert np.linalg.norm(v - r["v"]) <= 1e-5 * np.linalg.norm(r["v"])
+        p.close()

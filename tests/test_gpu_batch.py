@@ -316,7 +316,12 @@ def test_uniform_persistent_decode_bit_identical(s4, precision):
     rb = [t.clone() for t in b.execute_batched(xs)]
     for u, w in zip(ra, rb):
         assert torch.equal(u, w)
-    assert a.info["kernels_per_execute"] < b.info["kernels_per_execute"]
+    # the persistent decode replaces the per-iteration decodes where every iteration's DFT
+    # runs before the first decode (BF16x3); FP32 keeps its DFT-decode overlap
+    if precision == "bf16x3":
+        assert a.info["kernels_per_execute"] < b.info["kernels_per_execute"]
+    else:
+        assert a.info["kernels_per_execute"] == b.info["kernels_per_execute"]
     a.sync_status()
     a.close()
     b.close()

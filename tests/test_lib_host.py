@@ -48,14 +48,15 @@ def test_struct_layouts_match_c(tmp_path):
     from paper_2011_05698_gb300 import _lib
     src = tmp_path / "sz.c"
     src.write_text('#include "sfft4.h"\n#include <stdio.h>\n#include <stddef.h>\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(sfft4_opts), '
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(sfft4_opts), '
                    'sizeof(sfft4_plan_info), sizeof(sfft4_iter_info), offsetof(sfft4_iter_info, tau), '
                    'offsetof(sfft4_iter_info, unique_samples), sizeof(sfft4_c128), '
                    'offsetof(sfft4_opts, graph), sizeof(sfft4_batch_info), '
                    'offsetof(sfft4_batch_info, samples_per_execute), sizeof(sfft4_run_stats), '
                    'offsetof(sfft4_run_stats, votes_hist), offsetof(sfft4_opts, location), '
                    'offsetof(sfft4_opts, fold_order), offsetof(sfft4_opts, trace_signal), '
-                   'offsetof(sfft4_opts, batch_exec), offsetof(sfft4_opts, decode_cluster)); return 0;}\n')
+                   'offsetof(sfft4_opts, batch_exec), offsetof(sfft4_opts, fold_rounds), '
+                   'offsetof(sfft4_opts, decode_cluster)); return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
@@ -64,7 +65,7 @@ def test_struct_layouts_match_c(tmp_path):
             _lib.Opts.graph.offset, ctypes.sizeof(_lib.BatchInfo), _lib.BatchInfo.samples_per_execute.offset,
             ctypes.sizeof(_lib.RunStats), _lib.RunStats.votes_hist.offset, _lib.Opts.location.offset,
             _lib.Opts.fold_order.offset, _lib.Opts.trace_signal.offset, _lib.Opts.batch_exec.offset,
-            _lib.Opts.decode_cluster.offset]
+            _lib.Opts.fold_rounds.offset, _lib.Opts.decode_cluster.offset]
     assert got == want
 
 
@@ -106,7 +107,8 @@ def test_plan_rejects_bad_options(lib):
     from paper_2011_05698_gb300 import _lib
     for field, val in [("delta", 0.7), ("precision", 7), ("max_batch", -1), ("mag_tol", -1.0),
                        ("location", 3), ("fold_order", 2), ("fold_order", -1), ("decode_cluster", 3),
-                       ("decode_cluster", 32), ("decode_cluster", -1), ("batch_exec", 2), ("batch_exec", -1)]:
+                       ("decode_cluster", 32), ("decode_cluster", -1), ("batch_exec", 2), ("batch_exec", -1),
+                       ("fold_residues", 8), ("fold_residues", 48), ("fold_rounds", 9), ("fold_rounds", -1)]:
         o = _lib.Opts()
         lib.sfft4_opts_default(ctypes.byref(o))
         setattr(o, field, val)
