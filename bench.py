@@ -780,9 +780,24 @@ def main():
         ee = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist, dev)
         h2d = Se * N_DEF * 8
         d2h = sum(t.numel() * t.element_size() for t in oute)
+        # the host -> device link alone: the same pinned batch copied with nothing beside it
+        # (the copy engine and a zero-copy kernel both settle at this rate on a GB300)
+        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        link_s = []
+        for _ in range(3):
+            l0.record(copy_stream)
+            with torch.cuda.stream(copy_stream):
+                dx[0].copy_(host_x[0], non_blocking=True)
+            l1.record(copy_stream)
+            l1.synchronize()
+            link_s.append(l0.elapsed_time(l1) / 1e3)
+        link_gbs = h2d / min(link_s) / 1e9
         e2e = {"value": Se * esteps * world / ee, "unit": "transforms/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "batch": Se, "steps": esteps,
-               "h2d_gbs": h2d * esteps / ee / 1e9,
+               "h2d_gbs": h2d * esteps / ee / 1e9, "h2d_link_gbs": link_gbs,
+               "frac_of_link": h2d * esteps / ee / 1e9 / link_gbs,
+               "bound": "host -> device link (every signal's 8 N bytes cross it)",
                "form": "pinned host batch -> device copy (copy stream, double-buffered) + "
                        "sfft4_execute_batched + results -> pinned host, every step"}
         plan_e.close()

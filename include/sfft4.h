@@ -130,10 +130,10 @@ typedef struct {
                                 bit); an autotuner may pick them per (N, K)                 */
     int32_t decode_cluster;  /* CTAs that decode one signal (a thread-block cluster of 1, 2,
                                 4, 8 or 16 CTAs sharing the update's buckets and the
-                                candidates); 0 (default) = the largest power of two up to 8
-                                with which the execute's decode CTAs fit on the SMs (one
-                                signal: 8; batches of 152 or more signals: 1).  The results
-                                do not depend on it                                         */
+                                candidates); 0 (default) = the largest power of two up to 4
+                                with which the execute's decode CTAs fit on the SMs (up to
+                                38 signals: 4; up to 76: 2; more: 1).  The results do not
+                                depend on it                                         */
 } sfft4_opts;
 
 /* Fills *opts with the defaults above.  Returns SFFT4_EINVAL if opts is NULL. */

@@ -60,7 +60,7 @@ def test_cluster_sizes_bit_identical(s4, name, snr):
     sig = sparse_signal(N, K, 41, snr)
     x = to_dev(sig.x)
     ref = run(s4, name, x, 41, 1)
-    for c in (2, 8, 16):
+    for c in (2, 4, 8, 16):
         got = run(s4, name, x, 41, c)
         for u, w in zip(ref, got):
             assert torch.equal(u, w), (name, snr, c)
@@ -83,7 +83,8 @@ def test_cluster_decode_matches_oracle(s4, name, snr, seeds):
     N, K, l, q, B1 = CASES[name]
     for seed in seeds:
         sig = sparse_signal(N, K, seed, snr)
-        p = s4.Plan(N, K, l, q, seed=seed, B1=B1, decode_cluster=8, trace=True)
+        # the default (4 CTAs for one signal) on even seeds, 8 CTAs on odd ones
+        p = s4.Plan(N, K, l, q, seed=seed, B1=B1, decode_cluster=(0, 8)[seed % 2], trace=True)
         idx, val, nf, votes = p.execute(to_dev(sig.x))
         n = int(nf.item())
         f, v, vt = idx[:n].cpu().numpy(), val[:n].cpu().numpy(), votes[:n].cpu().numpy()
