@@ -1,6 +1,7 @@
 """Helpers shared by the GPU parity tests: fragile-decision detection and the replay that
 explains where a GPU run and the oracle part (the oracle's decode, fed the GPU's own bucket
-arrays and found set, must reproduce the GPU at the first iteration where they differ)."""
+arrays and found set, must reproduce the GPU at the first iteration where they differ, up to
+decisions of the replay itself within a fragile margin)."""
 
 import numpy as np
 
@@ -16,6 +17,32 @@ def fragile(tr):
         return True
     loc = tr["loc"]
     return loc is not None and (np.any(loc["margin"] < FRAGILE_TURNS) or np.any(loc["mag_margin"] < FRAGILE_REL))
+
+
+def replay_explains(out, rt, f_gpu, sigma, N):
+    """True when the oracle's replay of one iteration (found set `out`, trace `rt`, decoded
+    from the GPU's own bucket arrays) reproduces the GPU's found set `f_gpu`, or differs from
+    it only where the replay itself decided within a fragile margin.  The two decoders then
+    saw identical inputs and parted at a decision closer to its threshold than the FP32
+    arithmetic of the GPU resolves: a candidate's location or vote within FRAGILE_TURNS of a
+    block boundary or of H_s, or its magnitude test within FRAGILE_REL; or a selection within
+    FRAGILE_REL of the n_c-th bucket or of theta (one bucket swapped: at most two
+    frequencies differ)."""
+    got = [int(x) for x in f_gpu]
+    if list(out.f) == got:
+        return True
+    diff = set(int(x) for x in out.f) ^ set(got)
+    if rt["sel_margin"] < FRAGILE_REL and len(diff) <= 2:
+        return True
+    loc = rt["loc"]
+    if loc is None:
+        return False
+    fr = (pow(int(sigma), -1, N) * loc["ustar"]) % N
+    for e in diff:
+        k = np.flatnonzero(fr == e)
+        if k.size == 0 or not np.any((loc["margin"][k] < FRAGILE_TURNS) | (loc["mag_margin"][k] < FRAGILE_REL)):
+            return False
+    return True
 
 
 def found_set_from(f, v, vt):
@@ -44,8 +71,8 @@ def explain_divergence(p, r, N, K, l, q, seed, B1=0, signal=0):
         it = op.iters[tr["m"] - 1]
         sigma, a = philox.permutation_draw(seed, signal, it.m, N)
         _, _, Ghat = wc.get(it.B)
-        out, _ = O.decode_iteration(Y.astype(np.complex128), prev, it, op, sigma, a, r["theta"], Ghat)
-        assert list(out.f) == [int(x) for x in f], ("replay does not reproduce the GPU", tr["m"])
+        out, rt = O.decode_iteration(Y.astype(np.complex128), prev, it, op, sigma, a, r["theta"], Ghat)
+        assert replay_explains(out, rt, f, sigma, N), ("replay does not reproduce the GPU", tr["m"])
         return tr["m"]
     return None
 

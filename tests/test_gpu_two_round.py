@@ -77,7 +77,7 @@ def explain_two_round(p, r, N, K, l, q, seed):
         it = op.iters[tr["m"] - 1]
         sigma, a = philox.permutation_draw(seed, 0, it.m, N)
         _, _, Ghat = wc.get(it.B)
-        out, _ = O.decode_iteration(Y.astype(np.complex128), prev, it, op, sigma, a, r["theta"], Ghat)
-        assert list(out.f) == [int(x) for x in f], ("replay does not reproduce the GPU", tr["m"])
+        out, rt = O.decode_iteration(Y.astype(np.complex128), prev, it, op, sigma, a, r["theta"], Ghat)
+        assert PH.replay_explains(out, rt, f, sigma, N), ("replay does not reproduce the GPU", tr["m"])
         return tr["m"]
     return None
