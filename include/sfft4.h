@@ -122,7 +122,7 @@ typedef struct {
                                 m of every signal that has one), the decode chain on a second
                                 stream.  The results are identical                          */
     int32_t fold_residues;   /* fold tile shape: residues mod B per fold CTA (16, 32 or 64,
-                                at most B); default 32                                      */
+                                at most B); default 64                                      */
     int32_t fold_rounds;     /* fold tile shape: most rounds one fold CTA accumulates (1..8;
                                 an iteration's rounds are split into balanced groups of at
                                 most this many); default 6.  Both change the order of the

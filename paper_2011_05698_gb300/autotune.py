@@ -77,9 +77,9 @@ def saturating_batch(N):
     return int(min(512, max(8, (1 << 27) // N)))
 
 
-RESIDUES = (16, 32, 64)      # residues mod B per fold CTA; default 32
+RESIDUES = (16, 32, 64)      # residues mod B per fold CTA; default 64
 ROUNDS = (4, 6, 8)           # most rounds per fold group; default 6
-DEFAULT_SHAPE = (32, 6)
+DEFAULT_SHAPE = (64, 6)
 
 
 def _time_plan(N, K, l, q, precision, xs, supports, seed, reps, **kw):

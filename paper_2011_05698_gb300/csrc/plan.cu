@@ -315,10 +315,11 @@ int plan_schedule(sfft4_plan_s* p) {
             d.tau[s + 1] = ts;
         }
         // fold groups of up to kFoldRG rounds
-        // residues per fold CTA: 32 (measured against 16 and 64: small enough that the
-        // CTAs resident at a time cover few signals in signal-major order; one warp's window
-        // coefficient loads are then 32 contiguous floats)
-        ih.Wj = (int32_t)std::min<int64_t>(B, p->o.fold_residues ? p->o.fold_residues : 32);
+        // residues per fold CTA: 64 (with 512 threads, 8 copies of each residue).  Measured
+        // at 256 x (N = 2^22, K = 1000) on one GB300: 100.3 K transforms/s against 97.5 K with
+        // 32 residues (16 copies); 128 residues were slower still.  Two warps' window
+        // coefficient loads are 64 contiguous floats.
+        ih.Wj = (int32_t)std::min<int64_t>(B, p->o.fold_residues ? p->o.fold_residues : 64);
         ih.unique = 0;
         // balanced groups of at most kFoldGroupMax rounds (the fold kernel's accumulator count
         // is the largest group of its launch)
@@ -327,8 +328,13 @@ int plan_schedule(sfft4_plan_s* p) {
         for (int r0 = 0; r0 < d.R; r0 += gsz) {
             FoldGroup g;
             build_group(&g, d.tau, r0, std::min(gsz, d.R - r0), d.h);
-            int64_t per = (g.unique + B * 12 - 1) / (B * 12);
-            g.P = (int32_t)std::max<int64_t>(1, std::min<int64_t>(512 / ih.Wj, per));
+            // P copies of each residue: every fold CTA has 512 threads (Wj residues x P), the
+            // same in every job of a launch, so no thread of a launch sized by its largest job
+            // idles.  Measured at 256 x (N = 2^22, K = 1000): 90.1 K transforms/s, against
+            // 84.7 K with P sized for about 12 samples per thread (the B = 2048 tiles then
+            // used 320 of the launch's 448 threads), 88.2 K with 384 and 75.4 K with 256
+            // threads per tile.
+            g.P = (int32_t)std::max<int64_t>(1, 512 / ih.Wj);
             ih.groups.push_back(g);
         }
         {
