@@ -224,6 +224,37 @@ SFFT4_API int sfft4_execute_batched_async(sfft4_plan_t plan, int32_t nsig, const
 SFFT4_API int sfft4_wait(sfft4_plan_t plan, void* stream);
 
 /*
+ * sfft4_execute_batched_host -- sfft4_execute_batched_async (Section 2.1's problem for every
+ * signal, by the iterations of Section 3.1) on HOST buffers: the inputs are read from
+ * page-locked host memory into the workspace's device copy by a kernel of the library
+ * (zero-copy loads over the host link by 32 CTAs, which leave the other SMs to the
+ * transforms of the batch before), the batch runs as an asynchronous execute, and the
+ * results are copied back into the host outputs.  Consecutive calls overlap like
+ * asynchronous executes (two workspaces in turn), so one batch's inputs cross the link while
+ * the previous batch computes.
+ *   x_host      nsig * x_stride complex64 elements in page-locked host memory (cudaHostAlloc,
+ *               cudaMallocHost or cudaHostRegister; mapped, which unified addressing makes
+ *               every page-locked allocation); signal i starts at x_host + i * x_stride
+ *               (x_stride >= N).  16-byte aligned rows (even x_stride, 16-byte aligned
+ *               x_host) are read 16 bytes at a time, others 8.
+ *   idx_host, val_host, nfound_host, votes_host (may be NULL): as the device outputs of
+ *               sfft4_execute_batched, in host memory; page-locked keeps the call
+ *               asynchronous (pageable outputs are copied synchronously by the driver).
+ *   Results are complete once sfft4_wait(plan, s) has been issued on a stream s and s has
+ *   reached that point; x_host and the outputs of a call must stay valid and unmodified
+ *   until then, and calls in flight together need distinct output buffers.
+ *   The first host-buffer execute on each workspace allocates device copies of max_batch
+ *   inputs and outputs (max_batch * N * 8 bytes, plus the outputs), kept until
+ *   sfft4_destroy.
+ * Errors: SFFT4_EINVAL (NULL pointers, sizes as sfft4_execute_batched, x_host not
+ * page-locked host memory), SFFT4_ESTATE (a plan of sfft4_plan_batched, or opts.trace set),
+ * SFFT4_ENOMEM, SFFT4_ECUDA.
+ */
+SFFT4_API int sfft4_execute_batched_host(sfft4_plan_t plan, int32_t nsig, const void* x_host, int64_t x_stride,
+                                         int64_t* idx_host, sfft4_c128* val_host, int64_t* nfound_host,
+                                         int8_t* votes_host, void* stream);
+
+/*
  * sfft4_plan_batched -- plan of nsig transforms of different sizes, executed together
  * (batch of independent problems; each signal follows its own static schedule of Section 3.1).
  *   N[i], K[i]  size and sparsity of signal i, each within sfft4_plan's limits

@@ -223,6 +223,36 @@ class Plan:
                                        _stream_ptr(self.device)), fn)
         return idx, val, nf, votes
 
+    def host_outputs(self, nsig):
+        """Page-locked host output buffers (idx, val, nfound, votes) for execute_batched_host."""
+        import torch
+        K = self.K
+        return (torch.empty((nsig, K), dtype=torch.int64, pin_memory=True),
+                torch.empty((nsig, K), dtype=torch.complex128, pin_memory=True),
+                torch.empty((nsig,), dtype=torch.int64, pin_memory=True),
+                torch.empty((nsig, K), dtype=torch.int8, pin_memory=True))
+
+    def execute_batched_host(self, xs, out=None):
+        """Transforms of each row of xs, a page-locked (pinned) CPU complex64 tensor of shape
+        (nsig, N): the library stages the rows into device memory, runs them as an asynchronous
+        execute and copies the results into the host outputs (pinned CPU tensors, see
+        host_outputs).  Consecutive calls overlap; results are complete after wait() and a
+        synchronize of the current stream.  xs and the outputs must stay untouched until then."""
+        import torch
+        if not isinstance(xs, torch.Tensor) or xs.device.type != "cpu" or xs.dtype != torch.complex64:
+            raise TypeError("xs must be a CPU complex64 tensor")
+        if xs.dim() != 2 or xs.shape[-1] != self.N or xs.stride(-1) != 1:
+            raise ValueError(f"xs must have shape (nsig, {self.N}) and unit inner stride")
+        if not xs.is_pinned():
+            raise ValueError("xs must be in page-locked (pinned) host memory")
+        nsig = xs.shape[0]
+        idx, val, nf, votes = out if out is not None else self.host_outputs(nsig)
+        check(_lib.load().sfft4_execute_batched_host(self._h, nsig, ctypes.c_void_p(xs.data_ptr()), xs.stride(0),
+                                                     ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(val.data_ptr()),
+                                                     ctypes.c_void_p(nf.data_ptr()), ctypes.c_void_p(votes.data_ptr()),
+                                                     _stream_ptr(self.device)), "sfft4_execute_batched_host")
+        return idx, val, nf, votes
+
     def wait(self):
         """Makes the current stream wait for every asynchronous execute issued so far."""
         check(_lib.load().sfft4_wait(self._h, _stream_ptr(self.device)), "sfft4_wait")

@@ -87,6 +87,7 @@ SIGNATURES = [
     ("sfft4_execute_batched", ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, _P, _P, _P, _P, _P]),
     ("sfft4_execute_batched_async", ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, _P, _P, _P, _P, _P]),
     ("sfft4_wait", ctypes.c_int, [_P, _P]),
+    ("sfft4_execute_batched_host", ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, _P, _P, _P, _P, _P]),
     ("sfft4_plan_batched", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
                                           ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
                                           ctypes.c_int32, ctypes.c_double, ctypes.c_uint64, ctypes.POINTER(Opts)]),

@@ -2116,6 +2116,13 @@ int run(sfft4_plan_s* p, int nsig, const float2* x, int64_t x_stride, int64_t* i
 }
 }  // namespace
 
+namespace sfft4 {
+int run_execute(sfft4_plan_s* p, int nsig, const float2* x, int64_t x_stride, int64_t* idx,
+                sfft4_c128* val, int64_t* nfound, int8_t* votes, cudaStream_t st) {
+    return run(p, nsig, x, x_stride, idx, val, nfound, votes, st);
+}
+}  // namespace sfft4
+
 extern "C" {
 
 int sfft4_execute(sfft4_plan_t p, const void* x_dev, int64_t* idx_dev, sfft4_c128* val_dev,

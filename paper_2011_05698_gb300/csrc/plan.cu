@@ -100,7 +100,7 @@ void free_plan(sfft4_plan_s* p) {
         }
     }
     void* bufs[] = {p->dec_iters, p->queue, p->iters_dev, p->z, p->zall, p->uall, p->y, p->u, p->status, p->F, p->ff, p->fv, p->fvotes, p->hkeys,
-                    p->hvals, p->theta, p->fxexp, p->trace_y, p->trace_F, p->trace_ff,
+                    p->hvals, p->theta, p->fxexp, p->hx, p->hidx, p->hval, p->hnf, p->hvotes, p->trace_y, p->trace_F, p->trace_ff,
                     p->trace_fv, p->trace_votes};
     for (void* b : bufs) cudaFree(b);
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
@@ -115,6 +115,9 @@ void free_plan(sfft4_plan_s* p) {
         if (p->astream[s]) cudaStreamDestroy(p->astream[s]);
     }
     if (p->ev_sync) cudaEventDestroy(p->ev_sync);
+    for (cudaEvent_t e : p->ev_staged)
+        if (e) cudaEventDestroy(e);
+    if (p->hstream) cudaStreamDestroy(p->hstream);
     for (sfft4_plan_s* q : p->peer) free_plan(q);
     sfft4::destroy_group(p->grp);
     delete p;

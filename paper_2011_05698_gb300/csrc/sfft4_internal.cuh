@@ -255,6 +255,17 @@ struct sfft4_plan_s {
     // the caller's stream; an asynchronous execute that takes slot 0 waits for it
     cudaEvent_t ev_sync = nullptr;
     bool sync_pending = false;
+    // host-buffer executes (sfft4_execute_batched_host): device copies of max_batch inputs
+    // (dense rows of N) and outputs, allocated by the first such execute on this workspace
+    float2* hx = nullptr;
+    int64_t* hidx = nullptr;
+    sfft4_c128* hval = nullptr;
+    int64_t* hnf = nullptr;
+    int8_t* hvotes = nullptr;
+    // the stagings of consecutive host-buffer executes, one after another on their own stream
+    // (the host link stays busy); ev_staged[s] marks slot s's latest staging
+    cudaStream_t hstream = nullptr;
+    cudaEvent_t ev_staged[sfft4::kAsyncDepth] = {};
     int32_t* status = nullptr;  // 1 when a bounded device wait gave up
     int sm_count = 0;
     // persistent decode of a signal-major batch (opts.batch_exec): every iteration's decode
@@ -321,6 +332,9 @@ int build_signal_major_fold(sfft4_plan_s* p);
 // after the execute reads its inputs behind the work queued on `caller`; async_end marks it.
 int async_begin(sfft4_plan_s* p, cudaStream_t caller, sfft4_plan_s** w, cudaStream_t* as);
 int async_end(sfft4_plan_s* p, cudaStream_t as);
+// One execute of nsig signals on workspace p (stream st): the body of every execute entry.
+int run_execute(sfft4_plan_s* p, int nsig, const float2* x, int64_t x_stride, int64_t* idx,
+                sfft4_c128* val, int64_t* nfound, int8_t* votes, cudaStream_t st);
 // A synchronous execute waits for the asynchronous one that used the plan's own workspace;
 // mark_sync records its end, which the next asynchronous execute in slot 0 waits for.
 int join_slot0(sfft4_plan_s* p, cudaStream_t st);
