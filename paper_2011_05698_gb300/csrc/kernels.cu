@@ -173,7 +173,9 @@ int build_window_tables(sfft4_plan_s* p, Window* w, double delta) {
 
 // ----------------------------------------------------------------- fold -------------
 
-constexpr int kFoldUnroll = 4;
+// gathers in flight per thread (8 measured 1.2 % faster than 4 and 2 % faster than 2 with
+// tiles of 512 threads, about 15 samples per thread at B = 2048; no spills)
+constexpr int kFoldUnroll = 8;
 
 // One CTA = (signal, slice of Wj residues mod B).  Thread (jj, p) owns the samples
 // t = rho + m' B with rho = slice Wj + jj and m' = p (mod P), so its fold slot for round s,
