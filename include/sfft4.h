@@ -125,7 +125,7 @@ typedef struct {
                                 at most B); default 64                                      */
     int32_t fold_rounds;     /* fold tile shape: most rounds one fold CTA accumulates (1..8;
                                 an iteration's rounds are split into balanced groups of at
-                                most this many); default 6.  Both change the order of the
+                                most this many); default 3 (6 for sfft4_plan_batched).  Both change the order of the
                                 fold's sums (results agree to FP32 rounding, not bit for
                                 bit); an autotuner may pick them per (N, K)                 */
     int32_t decode_cluster;  /* CTAs that decode one signal (a thread-block cluster of 1, 2,

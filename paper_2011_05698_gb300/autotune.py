@@ -78,8 +78,13 @@ def saturating_batch(N):
 
 
 RESIDUES = (16, 32, 64)      # residues mod B per fold CTA; default 64
-ROUNDS = (4, 6, 8)           # most rounds per fold group; default 6
-DEFAULT_SHAPE = (64, 6)
+ROUNDS = (2, 3, 4)           # most rounds per fold group; default 3
+DEFAULT_SHAPE = (64, 3)
+# Rounds per fold group of a batch of uneven signals (the library's default for
+# sfft4_plan_batched): measured on the whole 512-signal batch of N = 2^16..2^22, 6 beat 3 and
+# 4 by 7-16 %, while the probe batches of a single (N, K) class prefer fewer rounds, so
+# choose() keeps 6 for batches and tunes only the residues there.
+BATCH_ROUNDS = 6
 
 
 def _time_plan(N, K, l, q, precision, xs, supports, seed, reps, **kw):
@@ -220,8 +225,8 @@ def choose_b1(Ns, Ks, l=16, q=1.0, precision="bf16x3", cache_path=None, device=N
 
 def choose(Ns, Ks, l=16, q=1.0, precision="bf16x3", cache_path=None, device=None, batch=None, log=None):
     """(B1 per signal, residues per fold CTA, rounds per fold group) for a batch: the fold's
-    tile shape is an option of the whole batch, so it is the shape tuned for the class that
-    carries the most samples (signals x N)."""
+    tile shape is an option of the whole batch, so the residues are those tuned for the class
+    that carries the most samples (signals x N), and the rounds per group BATCH_ROUNDS."""
     cache, key = _records(Ns, Ks, l, q, precision, cache_path, device, batch, log, shape_of_top=True)
     choose.last_seconds = _records.last_seconds
     weight = {}
@@ -229,4 +234,4 @@ def choose(Ns, Ks, l=16, q=1.0, precision="bf16x3", cache_path=None, device=None
         weight[key(N, K)] = weight.get(key(N, K), 0) + int(N)
     top = cache[max(weight, key=weight.get)]
     return ([cache[key(N, K)]["B1"] for N, K in zip(Ns, Ks)],
-            int(top.get("fold_residues", DEFAULT_SHAPE[0])), int(top.get("fold_rounds", DEFAULT_SHAPE[1])))
+            int(top.get("fold_residues", DEFAULT_SHAPE[0])), BATCH_ROUNDS)

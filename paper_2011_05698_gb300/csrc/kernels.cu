@@ -173,9 +173,9 @@ int build_window_tables(sfft4_plan_s* p, Window* w, double delta) {
 
 // ----------------------------------------------------------------- fold -------------
 
-// gathers in flight per thread (8 measured 1.2 % faster than 4 and 2 % faster than 2 with
-// tiles of 512 threads, about 15 samples per thread at B = 2048; no spills)
-constexpr int kFoldUnroll = 8;
+// gathers in flight per thread: with fold groups of at most 3 rounds, 4 measured 1.9 % faster
+// than 8 (with groups of 6 rounds 8 had been 1.2 % faster than 4); 16 spills
+constexpr int kFoldUnroll = 4;
 
 // One CTA = (signal, slice of Wj residues mod B).  Thread (jj, p) owns the samples
 // t = rho + m' B with rho = slice Wj + jj and m' = p (mod P), so its fold slot for round s,

@@ -508,12 +508,16 @@ int sfft4_plan_batched(sfft4_plan_t* out, int32_t nsig, const int64_t* N, const 
     if (!out) return SFFT4_EINVAL;
     *out = nullptr;
     if (nsig < 1 || !N || !K) return SFFT4_EINVAL;
+    // the batch's options, with its own default fold group size
+    sfft4_opts ob;
+    if (opts) ob = *opts;
+    else sfft4_opts_default(&ob);
+    if (ob.fold_rounds == 0) ob.fold_rounds = kFoldGroupMaxBatched;
+    opts = &ob;
     sfft4_opts o;
     int qn = 0;
     for (int32_t i = 0; i < nsig; ++i) {
-        sfft4_opts oi;
-        if (opts) oi = *opts;
-        else sfft4_opts_default(&oi);
+        sfft4_opts oi = ob;
         if (B1) oi.B1 = B1[i];
         int rc0 = plan_options(N[i], K[i], l, q, &oi, &o, &qn);
         if (rc0) return rc0;
@@ -537,8 +541,7 @@ int sfft4_plan_batched(sfft4_plan_t* out, int32_t nsig, const int64_t* N, const 
     p->bK.assign(K, K + nsig);
     if (B1) p->bB1.assign(B1, B1 + nsig);
     p->bq = q;
-    if (opts) p->bopts = *opts;
-    else sfft4_opts_default(&p->bopts);
+    p->bopts = ob;
     CK(cudaStreamCreateWithFlags(&p->dstream, cudaStreamNonBlocking));
     p->ev.assign(group_levels(p->grp) + 2, nullptr);
     for (auto& e : p->ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));

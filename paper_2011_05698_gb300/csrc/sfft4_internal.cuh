@@ -14,8 +14,11 @@ namespace sfft4 {
 
 constexpr int kMaxRounds = SFFT4_MAX_ROUNDS;  // R = S + 1 <= 64 rounds per iteration
 constexpr int kFoldRG = 8;                    // rounds accumulated per fold launch group
-constexpr int kFoldGroupMax = 6;              // rounds per fold group the planner forms (measured
-                                              // against 5 and 8 on N = 2^22, K = 1000)
+constexpr int kFoldGroupMax = 3;              // rounds per fold group the planner forms (measured
+                                              // against 2, 4, 5, 6 and 7 on N = 2^22, K = 1000)
+constexpr int kFoldGroupMaxBatched = 6;       // the same for sfft4_plan_batched (a 512-signal batch
+                                              // of N = 2^16..2^22: 189-194 K transforms/s
+                                              // pipelined with 6, 178 K with 4, 163-167 K with 3)
 constexpr int kMaxSeg = 2 * kFoldRG + 2;      // t-segments of one fold group
 constexpr int kQDen = 256;                    // q = q_n / 256
 constexpr int kBMin = 16;
