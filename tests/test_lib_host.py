@@ -29,7 +29,8 @@ def test_header_declares_expected_entry_points():
     names = declared_functions()
     for need in ("sfft4_plan", "sfft4_execute", "sfft4_execute_batched", "sfft4_destroy",
                  "sfft4_strerror", "sfft4_get_plan_info", "sfft4_bucketize", "sfft4_plan_batched",
-                 "sfft4_execute_batched_v", "sfft4_get_batch_info"):
+                 "sfft4_execute_batched_v", "sfft4_get_batch_info", "sfft4_execute_batched_async",
+                 "sfft4_execute_batched_host", "sfft4_wait", "sfft4_window_noalloc"):
         assert need in names
 
 
@@ -142,6 +143,7 @@ def test_execute_rejects_null_arguments(lib):
     assert lib.sfft4_get_batch_info(None, None) == _lib.SFFT4_EINVAL
     assert lib.sfft4_stats(None, None) == _lib.SFFT4_EINVAL
     assert lib.sfft4_execute_batched_async(None, 1, None, 0, None, None, None, None, None) == _lib.SFFT4_EINVAL
+    assert lib.sfft4_execute_batched_host(None, 1, None, 0, None, None, None, None, None) == _lib.SFFT4_EINVAL
     assert lib.sfft4_wait(None, None) == _lib.SFFT4_EINVAL
     assert lib.sfft4_execute_batched_v_async(None, None, None, None, None, None, None) == _lib.SFFT4_EINVAL
     assert lib.sfft4_sync_status(None) == _lib.SFFT4_EINVAL
