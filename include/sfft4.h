@@ -122,12 +122,15 @@ typedef struct {
                                 m of every signal that has one), the decode chain on a second
                                 stream.  The results are identical                          */
     int32_t fold_residues;   /* fold tile shape: residues mod B per fold CTA (16, 32 or 64,
-                                at most B); default 64                                      */
+                                at most B); default 64.  It sets the copies per residue and
+                                so the order of the fold's copy sums (results agree to FP32
+                                rounding, not bit for bit)                                  */
     int32_t fold_rounds;     /* fold tile shape: most rounds one fold CTA accumulates (1..8;
                                 an iteration's rounds are split into balanced groups of at
-                                most this many); default 3 (6 for sfft4_plan_batched).  Both change the order of the
-                                fold's sums (results agree to FP32 rounding, not bit for
-                                bit); an autotuner may pick them per (N, K)                 */
+                                most this many); default 3, 6 for sfft4_plan_batched.  It
+                                regroups the tiles only: every round's samples are still
+                                added in the same order.  An autotuner may pick both per
+                                (N, K)                                                      */
     int32_t decode_cluster;  /* CTAs that decode one signal (a thread-block cluster of 1, 2,
                                 4, 8 or 16 CTAs sharing the update's buckets and the
                                 candidates); 0 (default) = the largest power of two up to 4
