@@ -102,3 +102,29 @@ def test_signal_major_noiseless_matches_oracle(s4):
         assert np.array_equal(idx[i, :n], sig.freqs)
         assert np.linalg.norm(val[i, :n] - r["v"]) <= 1e-5 * np.linalg.norm(r["v"])
 
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_fold_rounds_regroup_without_changing_sums(s4, precision):
+    """opts.fold_rounds only regroups the fold's tiles (every thread still adds a round's
+    samples in increasing t, and the copies of a slot in copy order), so every bucket array
+    and every output is bit-identical whatever the group size, in both fold orders."""
+    import torch
+    N, K, l, q = 2**20, 100, 16, 1.0
+    xs = batch(N, K, [50, 51, 52], 20.0)
+    ref = None
+    for order in ("signal_major", "iteration_major"):
+        for rnd in (1, 3, 6, 8):
+            p = s4.Plan(N, K, l, q, seed=9, max_batch=3, precision=precision, fold_order=order, fold_rounds=rnd,
+                        trace=True, trace_signal=1)
+            out = [t.cpu() for t in p.execute_batched(xs)]
+            ys = [p.trace(m)[0] for m in range(1, p.info["n_iters"] + 1)]
+            p.sync_status()
+            p.close()
+            if ref is None:
+                ref = (out, ys)
+                continue
+            for u, w in zip(out, ref[0]):
+                assert torch.equal(u, w), (order, rnd)
+            for m, (u, w) in enumerate(zip(ys, ref[1])):
+                assert np.array_equal(u.view(np.uint32), w.view(np.uint32)), (order, rnd, m + 1)
