@@ -422,6 +422,13 @@ int build_group_plan(sfft4_plan_s* p, int nsig, const int64_t* Ns, const int64_t
 }
 
 namespace {
+
+// kernels launch_dft_tc_sets makes for these column sets (the profile counts each)
+int dft_set_launches(const std::vector<DftColSet>& sets) {
+    std::vector<int> Bs;
+    for (const auto& c : sets) Bs.push_back(c.B);
+    return dft_tc_launches(Bs.data(), (int)Bs.size());
+}
 struct GroupRun {
     const float2* const* x;
     int64_t* idx;
@@ -452,7 +459,7 @@ int group_body_persistent(sfft4_plan_s* p, const void* ctx, cudaStream_t st) {
                                      g->all_ycols + d.off, d.n});
         rc = prof_begin(p, st, &ev);
         if (!rc) rc = launch_dft_tc_sets(sets.data(), (int)sets.size(), p->status, p->sm_count, st);
-        if (!rc) rc = prof_end(p, st, ev, kProfFft, 0);
+        if (!rc) rc = prof_end(p, st, ev, kProfFft, 0, dft_set_launches(sets));
         if (rc) return rc;
     } else {
         for (const auto& d : g->all_dfts) {
@@ -502,7 +509,7 @@ int group_body(sfft4_plan_s* p, const void* ctx, cudaStream_t st) {
             cudaEvent_t ev = nullptr;
             rc = prof_begin(p, st, &ev);
             if (!rc) rc = launch_dft_tc_sets(sets.data(), (int)sets.size(), p->status, p->sm_count, st);
-            if (!rc) rc = prof_end(p, st, ev, kProfFft, 0);
+            if (!rc) rc = prof_end(p, st, ev, kProfFft, 0, dft_set_launches(sets));
             if (rc) return rc;
         } else {
             for (const auto& d : L.dfts) {

@@ -1482,7 +1482,8 @@ int launch_iter_dft(sfft4_plan_s* p, int mi, int nsig, const float2* z, int64_t 
         rc = check_cuda(cudaGetLastError());
     }
     if (rc) return rc;
-    return prof_end(p, st, ev, kProfFft, 0);
+    const int Bi = (int)B;
+    return prof_end(p, st, ev, kProfFft, 0, p->o.precision == SFFT4_BF16X3 ? dft_tc_launches(&Bi, 1) : 1);
 }
 
 int launch_bucketize(sfft4_plan_s* p, int mi, int nsig, const float2* x, int64_t x_stride,
@@ -1831,14 +1832,14 @@ int prof_begin(sfft4_plan_s* p, cudaStream_t st, cudaEvent_t* a) {
     return check_cuda(cudaEventRecord(*a, st));
 }
 
-int prof_end(sfft4_plan_s* p, cudaStream_t st, cudaEvent_t a, int kind, int64_t samples) {
+int prof_end(sfft4_plan_s* p, cudaStream_t st, cudaEvent_t a, int kind, int64_t samples, int launches) {
     if (!p->o.profile) return SFFT4_OK;
     cudaEvent_t b;
     int rc = next_event(p, &b);
     if (rc) return rc;
     rc = check_cuda(cudaEventRecord(b, st));
     if (rc) return rc;
-    p->prof.push_back({a, b, kind, samples});
+    p->prof.push_back({a, b, kind, samples, launches});
     return SFFT4_OK;
 }
 
@@ -2048,7 +2049,9 @@ int run_body(sfft4_plan_s* p, const void* ctx, cudaStream_t st) {
         cudaEvent_t ev = nullptr;
         rc = prof_begin(p, st, &ev);
         if (!rc) rc = launch_dft_tc_strided(sets.data(), (int)ni, p->status, p->sm_count, st);
-        if (!rc) rc = prof_end(p, st, ev, kProfFft, 0);
+        std::vector<int> Bs(ni);
+        for (size_t mi = 0; mi < ni; ++mi) Bs[mi] = (int)p->iters[mi].d.B;
+        if (!rc) rc = prof_end(p, st, ev, kProfFft, 0, dft_tc_launches(Bs.data(), (int)ni));
         if (!rc) rc = check_cuda(cudaEventRecord(p->ev[1], st));
         if (!rc) rc = check_cuda(cudaStreamWaitEvent(ds, p->ev[1], 0));
         if (rc) return rc;
@@ -2297,7 +2300,7 @@ int sfft4_profile_get(sfft4_plan_t p, sfft4_profile* out, int32_t reset) {
         switch (r.kind) {
             case kProfFold: p->prof_tot.fold_launches++; p->prof_tot.fold_ms += ms;
                             p->prof_tot.fold_samples += r.samples; break;
-            case kProfFft: p->prof_tot.fft_launches++; p->prof_tot.fft_ms += ms; break;
+            case kProfFft: p->prof_tot.fft_launches += r.launches; p->prof_tot.fft_ms += ms; break;
             case kProfDecode: p->prof_tot.decode_launches++; p->prof_tot.decode_ms += ms; break;
             default: p->prof_tot.finalize_launches++; p->prof_tot.finalize_ms += ms; break;
         }

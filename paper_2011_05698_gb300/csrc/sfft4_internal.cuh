@@ -305,6 +305,7 @@ struct sfft4_plan_s {
         cudaEvent_t a, b;
         int kind;
         int64_t samples;
+        int launches;  // kernels launched between a and b
     };
     std::vector<cudaEvent_t> ev_pool;
     std::vector<Prof> prof;
@@ -355,7 +356,7 @@ int launch_finalize_multi(const FinalJob* jobs, int nsig, int64_t Kout, int64_t*
                           int64_t* nfound, int8_t* votes, cudaStream_t st);
 int launch_votes_hist(const FinalJob* jobs, int nsig, unsigned long long* hist, cudaStream_t st);
 int prof_begin(sfft4_plan_s* p, cudaStream_t st, cudaEvent_t* a);
-int prof_end(sfft4_plan_s* p, cudaStream_t st, cudaEvent_t a, int kind, int64_t samples);
+int prof_end(sfft4_plan_s* p, cudaStream_t st, cudaEvent_t a, int kind, int64_t samples, int launches = 1);
 enum { kProfFold = 0, kProfFft = 1, kProfDecode = 2, kProfFinalize = 3 };
 int check_cuda(cudaError_t e);
 // Runs body(stream) directly, or (opts.graph) replays the graph captured from it for the
